@@ -1,0 +1,233 @@
+/*
+ * spd.h -- C ABI of the GB300 sparse tensor algebra kernels (libspd.so).
+ *
+ * The library executes the sparse kernels that SpDISTAL (Yadav, Aiken, Kjolstad,
+ * "SpDISTAL: Compiling Distributed Sparse Tensor Computations", arXiv 2207.13901)
+ * compiles, on one GPU:
+ *
+ *   SpMV      y(i)   = A(i,j) * x(j)                 Section VI-A
+ *   SpMM      Y(i,l) = A(i,j) * X(j,l)               Section VI-A (there A(i,j)=B(i,k)*C(k,j))
+ *   SpMM^T    dX(j,l)= A(i,j) * dY(i,l)              gradient of SpMM w.r.t. X (no paper counterpart)
+ *   SDDMM     A(i,j) = B(i,j) * C(i,k) * D(k,j)      Section VI-A
+ *   SpTTV     A(i,j) = B(i,j,k) * c(k)               Section VI-A
+ *   SpMTTKRP  A(i,l) = B(i,j,k) * C(j,l) * D(k,l)    Section VI-A
+ *
+ * Sparse operands use the Dense/Compressed level formats of Sections II-B and III-B:
+ * a Compressed level is a pair (pos, crd) where the children of parent entry i are at
+ * positions [pos[i], pos[i+1]) of crd. CSR = {Dense, Compressed};
+ * CSF = {Dense, Compressed, Compressed}. pos/crd are int32; pos[0] == 0, pos is
+ * non-decreasing, pos[last] == number of children, 0 <= crd < dimension. Coordinates
+ * need not be sorted within a segment and duplicates are summed like any other entry.
+ *
+ * Work is split in one of two ways (Section II-B, IV-B):
+ *   SPD_SPLIT_ROW  universe partition of the outer Dense level: piece c of P gets the
+ *                  outer coordinates [floor(c*n/P), floor((c+1)*n/P)); the inner levels
+ *                  follow by image (partitionFromParent).
+ *   SPD_SPLIT_NNZ  coordinate fusion of the levels plus a non-zero partition: the
+ *                  coordinate tree is flattened into one sequence of items (each outer
+ *                  entry's children followed by one "end of entry" item) and cut into
+ *                  pieces of equal item count; the outer level follows by preimage. Outer
+ *                  entries cut by a piece boundary are combined afterwards in binary64.
+ *   SPD_SPLIT_AUTO picks one of the two from the structure (currently SPD_SPLIT_NNZ).
+ *
+ * Common conventions for every compute call:
+ *   - All array arguments are DEVICE pointers owned by the caller. The library never
+ *     frees, retains or allocates them, and the compute calls allocate nothing: the
+ *     scratch space they need ("workspace") is passed in by the caller, sized by the
+ *     matching *_workspace_size call, and may be reused once the call's work on the
+ *     stream has finished.
+ *   - Outputs are overwritten (the paper's "+=" into a zeroed output).
+ *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL is the legacy default
+ *     stream) except the *_validate calls, which synchronize that stream.
+ *   - Argument errors are detected on the host before anything is launched and are
+ *     returned as an spd_status; nothing is written in that case. Structure errors
+ *     (a pos/crd that breaks the format) are NOT checked by the compute calls: run
+ *     spd_csr_validate / spd_csf3_validate once per structure.
+ *   - Dense matrices are row-major with an explicit leading dimension (in elements).
+ *   - Element types: values and dense inputs share one type t; results are binary64
+ *     when t is SPD_F64 and binary32 otherwise. SPD_F32/SPD_BF16 accumulate in
+ *     binary32, with compensated summation across tiles of one output row; pieces of a
+ *     row split across work units are combined in binary64.
+ *   - Pointers must be aligned to their element size; wider alignment (16 bytes) of
+ *     dense operands and leading dimensions enables vector loads.
+ */
+#ifndef SPD_H
+#define SPD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SPD_ABI_VERSION 1
+
+typedef enum {
+    SPD_OK = 0,
+    SPD_ERR_NULL = 1,      /* a required pointer is NULL */
+    SPD_ERR_SHAPE = 2,     /* a size is negative or sizes are inconsistent */
+    SPD_ERR_DTYPE = 3,     /* unsupported element type or type combination */
+    SPD_ERR_ALIGN = 4,     /* a pointer or leading dimension is misaligned */
+    SPD_ERR_STRUCTURE = 5, /* validate: the pos/crd arrays break the level format */
+    SPD_ERR_WORKSPACE = 6, /* workspace NULL or smaller than the size query returned */
+    SPD_ERR_CUDA = 7,      /* a CUDA runtime call or kernel launch failed */
+    SPD_ERR_OOM = 8,       /* reserved: the compute calls allocate nothing */
+    SPD_ERR_TIMEOUT = 9,   /* a bounded device-side wait gave up */
+    SPD_ERR_ARG = 10       /* an enum or tuning value is out of range */
+} spd_status;
+
+typedef enum { SPD_F64 = 0, SPD_F32 = 1, SPD_BF16 = 2 } spd_dtype;
+
+typedef enum { SPD_SPLIT_ROW = 0, SPD_SPLIT_NNZ = 1, SPD_SPLIT_AUTO = 2 } spd_split;
+
+typedef enum {
+    SPD_OP_SPMV = 0,
+    SPD_OP_SPMM = 1,
+    SPD_OP_SPMM_T = 2,
+    SPD_OP_SDDMM = 3,
+    SPD_OP_SPTTV = 4,
+    SPD_OP_SPMTTKRP = 5
+} spd_op;
+
+/* A CSR matrix {Dense, Compressed}: nrows x ncols with nnz stored entries.
+ * pos: int32[nrows+1], crd: int32[nnz], vals: nnz elements of type vtype (device). */
+typedef struct {
+    int64_t nrows, ncols, nnz;
+    const int32_t *pos;
+    const int32_t *crd;
+    const void *vals;
+    int32_t vtype; /* spd_dtype */
+    int32_t reserved;
+} spd_csr;
+
+/* A CSF 3-tensor {Dense, Compressed, Compressed} of shape dim0 x dim1 x dim2 with nfib
+ * non-empty fibers (i,j) and nnz stored entries.
+ * pos1: int32[dim0+1], crd1: int32[nfib] (j of each fiber),
+ * pos2: int32[nfib+1], crd2: int32[nnz] (k of each entry), vals: nnz elements. */
+typedef struct {
+    int64_t dim0, dim1, dim2;
+    int64_t nfib, nnz;
+    const int32_t *pos1;
+    const int32_t *crd1;
+    const int32_t *pos2;
+    const int32_t *crd2;
+    const void *vals;
+    int32_t vtype; /* spd_dtype */
+    int32_t reserved;
+} spd_csf3;
+
+/* Optional tuning (NULL = defaults). Zero fields take the default.
+ *   unit_items    items (children + end-of-entry marks) per work unit of SPD_SPLIT_NNZ
+ *                 for the warp-per-unit kernels (SpMM, SpMM^T, SDDMM, SpMTTKRP);
+ *                 must be a multiple of 32 in [32, 65536].
+ *   row_pieces    number of pieces P of SPD_SPLIT_ROW (1 <= P <= 2^31-1).
+ *   block_threads threads per block for the warp-per-unit kernels: 64..1024,
+ *                 multiple of 32. */
+typedef struct {
+    int32_t unit_items;
+    int32_t row_pieces;
+    int32_t block_threads;
+    int32_t reserved;
+} spd_tune;
+
+/* -------------------------------------------------------------------- misc */
+
+/* SPD_ABI_VERSION of the loaded library. */
+int spd_abi_version(void);
+
+/* Static English text for a status code (never NULL). */
+const char *spd_status_str(int status);
+
+/* Detail of the last error returned on the calling thread (static buffer of the
+ * thread; empty string when there is none). */
+const char *spd_last_error(void);
+
+/* -------------------------------------------------------------------- sizes */
+
+/* Workspace bytes that `op` on CSR `A` with `split` needs. `width` is L for SpMM and
+ * SpMM^T, K for SDDMM, ignored for SpMV. The result may be 0 (any pointer, even NULL,
+ * is then accepted as workspace). Host-only, no device access. */
+spd_status spd_csr_workspace_size(int op, const spd_csr *A, int split, int64_t width,
+                                  const spd_tune *tune, size_t *bytes);
+
+/* Same for the CSF operations (SPD_OP_SPTTV; SPD_OP_SPMTTKRP with width = R). */
+spd_status spd_csf3_workspace_size(int op, const spd_csf3 *B, int split, int64_t width,
+                                   const spd_tune *tune, size_t *bytes);
+
+/* -------------------------------------------------------------------- structure */
+
+/* Checks the level-format invariants of A (Section III-B): pos[0] == 0, pos
+ * non-decreasing, pos[nrows] == nnz, 0 <= crd < ncols. Needs a workspace of at least
+ * 64 bytes. Synchronizes `stream`. On return *violations holds the number of violated
+ * entries and *first_bad the smallest offending index (an index into pos, or
+ * nrows + 1 + p for crd position p), or -1 if there is none. Returns SPD_OK when the
+ * structure is valid, SPD_ERR_STRUCTURE when it is not. */
+spd_status spd_csr_validate(const spd_csr *A, void *ws, size_t ws_bytes, int64_t *violations,
+                            int64_t *first_bad, void *stream);
+
+/* The same checks on both Compressed levels of a CSF tensor: level 2 (pos1/crd1 against
+ * dim1, children nfib) then level 3 (pos2/crd2 against dim2, children nnz). first_bad
+ * indexes the concatenation pos1 | crd1 | pos2 | crd2. Synchronizes `stream`. */
+spd_status spd_csf3_validate(const spd_csf3 *B, void *ws, size_t ws_bytes, int64_t *violations,
+                             int64_t *first_bad, void *stream);
+
+/* Writes the work partition the compute calls use (Sections II-B, III-A, IV-C) into two
+ * device int32 arrays of length npieces+1:
+ *   SPD_SPLIT_ROW: rows_out[c] = floor(c*nrows/P) with P = npieces, pos_out[c] =
+ *                  pos[rows_out[c]] (the image of the row piece in crd).
+ *   SPD_SPLIT_NNZ: for the diagonals d_c = min(c*unit_items, nrows + nnz) of the
+ *                  flattened item sequence, rows_out[c] = number of rows whose end
+ *                  item lies before d_c and pos_out[c] = d_c - rows_out[c]; here
+ *                  npieces must equal ceil((nrows + nnz) / unit_items).
+ * unit_items is ignored for SPD_SPLIT_ROW. Asynchronous. */
+spd_status spd_csr_partition(const spd_csr *A, int split, int64_t npieces, int64_t unit_items,
+                             int32_t *rows_out, int32_t *pos_out, void *stream);
+
+/* -------------------------------------------------------------------- compute */
+
+/* SpMV y(i) = A(i,j) * x(j).  x: ncols elements of A->vtype; y: nrows elements of
+ * y_type (SPD_F64 for F64 values, SPD_F32 otherwise). */
+spd_status spd_spmv(const spd_csr *A, const void *x, int x_type, void *y, int y_type, int split,
+                    const spd_tune *tune, void *ws, size_t ws_bytes, void *stream);
+
+/* SpMM Y(i,l) = A(i,j) * X(j,l), l < L.  X: ncols x L (leading dimension ldx >= L) of
+ * x_type == A->vtype; Y: nrows x L (ldy >= L) of y_type. */
+spd_status spd_spmm(const spd_csr *A, const void *X, int64_t L, int64_t ldx, int x_type, void *Y,
+                    int64_t ldy, int y_type, int split, const spd_tune *tune, void *ws,
+                    size_t ws_bytes, void *stream);
+
+/* SpMM^T dX(j,l) = A(i,j) * dY(i,l): the gradient of Y = A X with respect to X, without
+ * forming A's transpose (rows of A are walked and scattered with atomic adds, so the
+ * summation order is not deterministic).  dY: nrows x L (ldy) of dy_type ==
+ * A->vtype; dX: ncols x L (ldx) of dx_type (F64 for F64, F32 otherwise). */
+spd_status spd_spmm_t(const spd_csr *A, const void *dY, int64_t L, int64_t ldy, int dy_type,
+                      void *dX, int64_t ldx, int dx_type, int split, const spd_tune *tune,
+                      void *ws, size_t ws_bytes, void *stream);
+
+/* SDDMM A(i,j) = B(i,j) * C(i,k) * D(k,j), k < K. The output keeps B's pattern
+ * (Section V-B): out_vals[p] is the value at B's position p, and B's pos/crd serve as
+ * the output's. B->vals may be NULL: every B value is then 1 (the sampling pattern).
+ * C: nrows x K (ldc); D is passed transposed, as Dnk: ncols x K (ldd) with
+ * Dnk[j,k] = D(k,j). C, Dnk (and B's values) have dense_type; out_vals has out_type. */
+spd_status spd_sddmm(const spd_csr *B, const void *C, int64_t K, int64_t ldc, const void *Dnk,
+                     int64_t ldd, int dense_type, void *out_vals, int out_type, int split,
+                     const spd_tune *tune, void *ws, size_t ws_bytes, void *stream);
+
+/* SpTTV A(i,j) = B(i,j,k) * c(k). The output keeps B's (i,j) structure (Section V-B):
+ * out_vals[f] belongs to fiber f, and B's pos1/crd1 serve as the output's pos/crd.
+ * c: dim2 elements of c_type == B->vtype. */
+spd_status spd_spttv(const spd_csf3 *B, const void *c, int c_type, void *out_vals, int out_type,
+                     int split, const spd_tune *tune, void *ws, size_t ws_bytes, void *stream);
+
+/* SpMTTKRP A(i,l) = B(i,j,k) * C(j,l) * D(k,l), l < R.  C: dim1 x R (ldc), D: dim2 x R
+ * (ldd) of factor_type == B->vtype; A: dim0 x R (lda) of a_type. */
+spd_status spd_spmttkrp(const spd_csf3 *B, const void *C, int64_t ldc, const void *D, int64_t ldd,
+                        int64_t R, int factor_type, void *A, int64_t lda, int a_type, int split,
+                        const spd_tune *tune, void *ws, size_t ws_bytes, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPD_H */

@@ -1,0 +1,13 @@
+"""GB300-native sparse tensor algebra kernels of SpDISTAL (arXiv 2207.13901).
+
+SpMV, SpMM, SpMM^T, SDDMM, SpTTV and SpMTTKRP over CSR {Dense, Compressed} and CSF
+{Dense, Compressed, Compressed} operands, split by rows (universe partition) or by
+nonzeros (coordinate fusion + non-zero partition), executed by hand-written sm_103a
+kernels behind the C ABI of include/spd.h. PyTorch supplies memory and streams.
+"""
+from .ops import (CSF3, CSR, csf3_workspace_size, csr_workspace_size, partition, result_dtype, sddmm, spmm, spmm_t,
+                  spmttkrp, spmv, spttv, validate)
+from . import autograd
+
+__all__ = ["CSR", "CSF3", "spmv", "spmm", "spmm_t", "sddmm", "spttv", "spmttkrp", "validate", "partition",
+           "csr_workspace_size", "csf3_workspace_size", "result_dtype", "autograd"]

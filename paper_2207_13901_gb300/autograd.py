@@ -1,0 +1,45 @@
+"""Differentiable SpMM: Y = A X with a hand-written backward.
+
+    forward   Y(i,l)  = A(i,j) X(j,l)                       (spd_spmm)
+    backward  dA(i,j) = dY(i,l) X(j,l) on A's pattern only  (spd_sddmm with B = pattern)
+              dX(j,l) = A(i,j) dY(i,l)                      (spd_spmm_t, no transpose formed)
+
+The gradient with respect to A's values is the sampled dense-dense product of dY and X
+on A's sparsity pattern, i.e. SDDMM (Section VI-A) with every B value equal to 1. The
+backward computes in A's value type: a binary32 gradient dY is rounded to bfloat16 when
+the values are bfloat16.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import ops
+
+
+class SpMMFunction(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, vals, X, pattern, split, tune):
+        A = pattern.with_vals(vals)
+        Y = ops.spmm(A, X, split=split, tune=tune)
+        ctx.save_for_backward(vals, X)
+        ctx.pattern = pattern
+        ctx.split = split
+        ctx.tune = tune
+        return Y
+
+    @staticmethod
+    def backward(ctx, dY):
+        vals, X = ctx.saved_tensors
+        dY = dY.to(vals.dtype).contiguous()
+        dvals = dX = None
+        if ctx.needs_input_grad[0]:
+            dvals = ops.sddmm(ctx.pattern.with_vals(None), dY, X, split=ctx.split, tune=ctx.tune).to(vals.dtype)
+        if ctx.needs_input_grad[1]:
+            A = ctx.pattern.with_vals(vals)
+            dX = ops.spmm_t(A, dY, split=ctx.split, tune=ctx.tune).to(X.dtype)
+        return dvals, dX, None, None, None
+
+
+def spmm(A: "ops.CSR", X: torch.Tensor, split: str = "nnz", tune=None) -> torch.Tensor:
+    """Y = A X, differentiable with respect to A.vals and X."""
+    return SpMMFunction.apply(A.vals, X, A.with_vals(None), split, tune)

@@ -1,0 +1,281 @@
+// spd_internal.cuh -- shared device helpers and host-side argument plumbing of libspd.
+//
+// Layout and vocabulary follow the level formats of Sections II-B and III-B of
+// SpDISTAL (arXiv 2207.13901): a Compressed level is (pos, crd) with the children of
+// parent entry i at positions [pos[i], pos[i+1]).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <climits>
+#include <cstdio>
+#include <cstring>
+
+#include "../../include/spd.h"
+
+namespace spd {
+
+// ------------------------------------------------------------------ element types
+
+template <typename VT> struct Traits;
+template <> struct Traits<double> {
+    using acc = double;  // accumulation type
+    using out = double;  // result type
+    static constexpr int code = SPD_F64;
+};
+template <> struct Traits<float> {
+    using acc = float;
+    using out = float;
+    static constexpr int code = SPD_F32;
+};
+template <> struct Traits<__nv_bfloat16> {
+    using acc = float;
+    using out = float;
+    static constexpr int code = SPD_BF16;
+};
+
+__device__ __forceinline__ float to_acc(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_acc(float v) { return v; }
+__device__ __forceinline__ double to_acc(double v) { return v; }
+
+// Streaming (evict-first) loads for data read exactly once: crd, vals, pos windows.
+__device__ __forceinline__ int32_t ld_stream(const int32_t *p) { return __ldcs(p); }
+__device__ __forceinline__ float ld_stream(const float *p) { return __ldcs(p); }
+__device__ __forceinline__ double ld_stream(const double *p) { return __ldcs(p); }
+__device__ __forceinline__ float ld_stream(const __nv_bfloat16 *p) { return __bfloat162float(__ldcs(p)); }
+
+// Cached loads for gathered dense operands (reused through L1/L2).
+__device__ __forceinline__ float ld_gather(const float *p) { return __ldg(p); }
+__device__ __forceinline__ double ld_gather(const double *p) { return __ldg(p); }
+__device__ __forceinline__ float ld_gather(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
+
+// Loads N consecutive elements starting at p (p aligned to N elements when N > 1)
+// and converts them to the accumulation type.
+template <int N>
+__device__ __forceinline__ void ld_vec(const float *p, float (&o)[N]) {
+    if constexpr (N == 1) {
+        o[0] = __ldg(p);
+    } else if constexpr (N == 2) {
+        float2 v = __ldg(reinterpret_cast<const float2 *>(p));
+        o[0] = v.x; o[1] = v.y;
+    } else {
+#pragma unroll
+        for (int q = 0; q < N / 4; ++q) {
+            float4 v = __ldg(reinterpret_cast<const float4 *>(p) + q);
+            o[4 * q + 0] = v.x; o[4 * q + 1] = v.y; o[4 * q + 2] = v.z; o[4 * q + 3] = v.w;
+        }
+    }
+}
+template <int N>
+__device__ __forceinline__ void ld_vec(const double *p, double (&o)[N]) {
+    if constexpr (N == 1) {
+        o[0] = __ldg(p);
+    } else {
+#pragma unroll
+        for (int q = 0; q < N / 2; ++q) {
+            double2 v = __ldg(reinterpret_cast<const double2 *>(p) + q);
+            o[2 * q + 0] = v.x; o[2 * q + 1] = v.y;
+        }
+    }
+}
+template <int N>
+__device__ __forceinline__ void ld_vec(const __nv_bfloat16 *p, float (&o)[N]) {
+    if constexpr (N == 1) {
+        o[0] = __bfloat162float(__ldg(p));
+    } else if constexpr (N == 2) {
+        float2 f = __bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162 *>(p)));
+        o[0] = f.x; o[1] = f.y;
+    } else if constexpr (N == 4) {
+        uint2 raw = __ldg(reinterpret_cast<const uint2 *>(p));
+        __nv_bfloat162 a = *reinterpret_cast<__nv_bfloat162 *>(&raw.x);
+        __nv_bfloat162 b = *reinterpret_cast<__nv_bfloat162 *>(&raw.y);
+        float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+        o[0] = fa.x; o[1] = fa.y; o[2] = fb.x; o[3] = fb.y;
+    } else {
+#pragma unroll
+        for (int q = 0; q < N / 8; ++q) {
+            uint4 raw = __ldg(reinterpret_cast<const uint4 *>(p) + q);
+            uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                float2 f = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&w[h]));
+                o[8 * q + 2 * h] = f.x;
+                o[8 * q + 2 * h + 1] = f.y;
+            }
+        }
+    }
+}
+
+// Stores N consecutive results (p aligned to N elements when N > 1), streaming.
+template <int N>
+__device__ __forceinline__ void st_vec(float *p, const float (&v)[N]) {
+    if constexpr (N == 1) {
+        __stcs(p, v[0]);
+    } else if constexpr (N == 2) {
+        __stcs(reinterpret_cast<float2 *>(p), make_float2(v[0], v[1]));
+    } else {
+#pragma unroll
+        for (int q = 0; q < N / 4; ++q)
+            __stcs(reinterpret_cast<float4 *>(p) + q, make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));
+    }
+}
+template <int N>
+__device__ __forceinline__ void st_vec(double *p, const double (&v)[N]) {
+    if constexpr (N == 1) {
+        __stcs(p, v[0]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < N / 2; ++q)
+            __stcs(reinterpret_cast<double2 *>(p) + q, make_double2(v[2 * q], v[2 * q + 1]));
+    }
+}
+
+// Compensated accumulation (Neumaier's variant of Kahan summation): hi + lo carries
+// the running sum; lo collects the rounding error of every addition.
+template <typename T>
+__device__ __forceinline__ void comp_add(T &hi, T &lo, T b) {
+    T s = hi + b;
+    if (fabs(hi) >= fabs(b)) lo += (hi - s) + b;
+    else lo += (b - s) + hi;
+    hi = s;
+}
+
+// ------------------------------------------------------------------ partitions
+
+// Merge-path state of the flattened coordinate tree: after d items, `rows` rows have
+// ended and `pos` children have been consumed (rows + pos == d). Row r's end item
+// sits at index pos[r+1] + r of the sequence (its children come first).
+struct PieceBounds {
+    int32_t r0, p0, r1, p1;
+};
+
+// Bounds of piece c of the universe (row) partition into P pieces:
+// rows [floor(c n / P), floor((c+1) n / P)) and, by image, positions [pos[r0], pos[r1]).
+__device__ __forceinline__ PieceBounds row_piece(int64_t c, int64_t P, int64_t n, const int32_t *pos) {
+    PieceBounds b;
+    b.r0 = (int32_t)((c * n) / P);
+    b.r1 = (int32_t)(((c + 1) * n) / P);
+    b.p0 = __ldg(pos + b.r0);
+    b.p1 = __ldg(pos + b.r1);
+    return b;
+}
+
+// Bounds of piece c of the fused non-zero partition, read from a partition array.
+__device__ __forceinline__ PieceBounds nnz_piece(int64_t c, const int32_t *prow, const int32_t *ppos) {
+    PieceBounds b;
+    b.r0 = __ldg(prow + c);
+    b.p0 = __ldg(ppos + c);
+    b.r1 = __ldg(prow + c + 1);
+    b.p1 = __ldg(ppos + c + 1);
+    return b;
+}
+
+// ------------------------------------------------------------------ host plumbing
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// Records an error detail for spd_last_error() and returns the status.
+spd_status fail(spd_status s, const char *fmt, ...);
+spd_status check_launch(const char *what);
+inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+inline bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+inline size_t dtype_size(int t) { return t == SPD_F64 ? 8 : t == SPD_F32 ? 4 : t == SPD_BF16 ? 2 : 0; }
+inline int result_type(int t) { return t == SPD_F64 ? SPD_F64 : SPD_F32; }
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+spd_status check_csr(const spd_csr *A, bool need_vals);
+spd_status check_csf3(const spd_csf3 *B);
+
+// Defaults shared by the size queries and the compute calls.
+constexpr int kSpmvThreads = 256;   // threads of the tile-per-block SpMV / SpTTV kernel
+constexpr int kSpmvIPT = 8;         // items per thread of one tile
+constexpr int kSpmvTile = kSpmvThreads * kSpmvIPT;
+constexpr int kWarpUnitDefault = 2048;  // items per warp unit (warp-per-unit kernels)
+constexpr int kWarpBlockDefault = 256;
+
+struct Tuning {
+    int64_t unit_items;   // warp-unit size of SPD_SPLIT_NNZ (warp kernels)
+    int64_t row_pieces;   // P of SPD_SPLIT_ROW (0 = per-kernel default)
+    int block_threads;    // threads per block (warp kernels)
+};
+spd_status read_tune(const spd_tune *t, Tuning *out);
+int resolve_split(int split);
+
+// Workspace of one partitioned call: the partition arrays (nnz split only) and the
+// binary64 carries of outer entries cut by piece boundaries.
+struct WsLayout {
+    int64_t npieces = 0;
+    size_t part_row = 0, part_pos = 0, part_aux = 0, carry_row = 0, carry_val = 0;
+    size_t total = 0;
+};
+// npieces pieces, `width` carried values per piece, `aux` = extra int32 per boundary.
+WsLayout make_layout(int64_t npieces, int64_t width, bool need_partition, bool need_carry, bool aux);
+
+// Launches the fused non-zero partition of a level (pos, n parents, nnz children) into
+// the boundary arrays prow/ppos (npieces + 1 entries each).
+spd_status launch_merge_partition(int64_t n, int64_t nnz, const int32_t *pos, int64_t unit,
+                                  int64_t npieces, int32_t *prow, int32_t *ppos, cudaStream_t st);
+
+// Workspace layouts of the calls (shared by the size queries and the compute calls).
+WsLayout layout_spmv(int64_t n, int64_t nnz, int split);
+WsLayout layout_warp(int64_t n, int64_t nnz, int split, int64_t unit, int64_t width, bool carries);
+WsLayout layout_mttkrp(int64_t F, int64_t nnz, int split, int64_t unit, int64_t R);
+
+spd_status check_ws(const WsLayout &L, void *ws, size_t ws_bytes);
+spd_status check_dense(const char *name, const void *p, int64_t rows, int64_t L, int64_t ld, int t);
+
+// Elements per lane for the warp kernels: the smallest power of two that lets 32 lanes
+// cover L, capped by a 32-byte vector, lowered until the pointers and leading
+// dimensions allow vector accesses of that width.
+int pick_epl(int64_t L, size_t in_size, size_t out_size, const void *in, int64_t ld_in, const void *out,
+             int64_t ld_out);
+
+// Zero rows x L of a row-major matrix with leading dimension lda (one warp per row).
+template <typename OT>
+__global__ void zero_rows_kernel(int64_t rows, int64_t L, OT *__restrict__ A, int64_t lda) {
+    const int64_t wstride = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < rows; i += wstride)
+        for (int64_t l = threadIdx.x & 31; l < L; l += 32) A[i * lda + l] = (OT)0;
+}
+
+template <typename OT>
+inline spd_status launch_zero_rows(int64_t rows, int64_t L, OT *A, int64_t lda, cudaStream_t st) {
+    if (rows <= 0 || L <= 0) return SPD_OK;
+    int64_t grid = ceil_div(rows, 8);
+    if (grid > 152 * 64) grid = 152 * 64;
+    zero_rows_kernel<OT><<<(unsigned)grid, 256, 0, st>>>(rows, L, A, lda);
+    return check_launch("zero_rows_kernel");
+}
+
+// Adds the binary64 carries of consecutive pieces that ended inside the same outer entry
+// (row or slice) to the value the completing piece wrote. One warp per piece, one lane
+// per column; only the first piece of each run does the work.
+template <typename OT>
+__global__ void carry_fixup_rows_kernel(int64_t npieces, int64_t L, const int32_t *__restrict__ carry_row,
+                                        const double *__restrict__ carry_val, OT *__restrict__ Y, int64_t ldy) {
+    const int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t col = (int64_t)blockIdx.y * 32 + (threadIdx.x & 31);
+    if (c >= npieces || col >= L) return;
+    const int32_t row = carry_row[c];
+    if (row < 0) return;
+    if (c > 0 && carry_row[c - 1] == row) return;
+    double s = 0.0;
+    for (int64_t d = c; d < npieces && carry_row[d] == row; ++d) s += carry_val[d * L + col];
+    OT *yp = Y + (int64_t)row * ldy + col;
+    *yp = (OT)((double)*yp + s);
+}
+
+template <typename OT>
+inline spd_status launch_carry_fixup(int64_t npieces, int64_t L, const int32_t *crow, const double *cval, OT *Y,
+                                     int64_t ldy, cudaStream_t st) {
+    if (npieces <= 0 || L <= 0) return SPD_OK;
+    dim3 grid((unsigned)ceil_div(npieces, 8), (unsigned)ceil_div(L, 32));
+    carry_fixup_rows_kernel<OT><<<grid, 256, 0, st>>>(npieces, L, crow, cval, Y, ldy);
+    return check_launch("carry_fixup_rows_kernel");
+}
+
+}  // namespace spd

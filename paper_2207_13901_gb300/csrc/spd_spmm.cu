@@ -1,0 +1,349 @@
+// spd_spmm.cu -- SpMM Y(i,l) = A(i,j) * X(j,l) (Section VI-A) and its gradient with
+// respect to X, SpMM^T dX(j,l) = A(i,j) * dY(i,l), without forming A's transpose.
+//
+// One warp consumes one piece of the flattened coordinate tree of A. The 32 lanes
+// span a tile of 32*EPL dense columns, so every nonzero costs one coalesced row of X
+// (a 16- or 32-byte vector per lane). crd/vals are streamed 32 at a time and broadcast
+// with shuffles; U rows of X are in flight before they are consumed. Row ends come
+// from a 32-entry window of pos held one entry per lane. A row is written once, when
+// its end item is reached; rows longer than 4096 nonzeros accumulate with compensated
+// (Kahan-Neumaier) summation in the binary32 modes. In the nnz split the partial row
+// at a piece end is stored as binary64 and added by a fix-up kernel.
+#include "spd_internal.cuh"
+
+namespace spd {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int32_t kLongRow = 4096;
+
+template <typename T, int N>
+__device__ __forceinline__ void zero(T (&a)[N]) {
+#pragma unroll
+    for (int e = 0; e < N; ++e) a[e] = (T)0;
+}
+
+// Window of row ends: lane q holds the end of row rw + q (true_end) while the warp
+// walks rows rw .. rw+31. Rows >= r1 are not completed by this piece.
+struct RowWindow {
+    int32_t rw;        // first row of the window
+    int32_t true_end;  // pos[rw + lane + 1] (or INT_MAX past n)
+    __device__ __forceinline__ void load(int32_t base, int64_t n, const int32_t *pos, int lane) {
+        rw = base;
+        int64_t q = (int64_t)base + lane;
+        true_end = q < n ? ld_stream(pos + q + 1) : INT_MAX;
+    }
+    __device__ __forceinline__ int32_t end_of(int32_t r) const { return __shfl_sync(FULL, true_end, r - rw); }
+};
+
+template <typename VT, int EPL, int U>
+__global__ void __launch_bounds__(256) spmm_warp_kernel(
+    int64_t n, const int32_t *__restrict__ pos, const int32_t *__restrict__ crd, const VT *__restrict__ vals,
+    const VT *__restrict__ X, int64_t ldx, typename Traits<VT>::out *__restrict__ Y, int64_t ldy, int64_t L,
+    const int32_t *__restrict__ prow, const int32_t *__restrict__ ppos, int64_t npieces, int64_t P,
+    int32_t *__restrict__ carry_row, double *__restrict__ carry_val) {
+    using AT = typename Traits<VT>::acc;
+    using OT = typename Traits<VT>::out;
+    const int lane = threadIdx.x & 31;
+    const int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (c >= (prow ? npieces : P)) return;  // whole warp
+    const int64_t col = (int64_t)blockIdx.y * (32 * EPL) + (int64_t)lane * EPL;
+    const bool active = col < L;
+    const PieceBounds b = prow ? nnz_piece(c, prow, ppos) : row_piece(c, P, n, pos);
+
+    AT acc[EPL], cmp[EPL];
+    zero(acc);
+    zero(cmp);
+    int32_t r = b.r0;
+    RowWindow win;
+    win.load(r, n, pos, lane);
+    int32_t cur_start = r < n ? __ldg(pos + r) : b.p1;
+    int32_t true_end = r < n ? win.end_of(r) : INT_MAX;
+    int32_t cur_end = r < b.r1 ? true_end : INT_MAX;
+    bool kahan = (sizeof(AT) == 4) && (true_end - cur_start > kLongRow);
+
+    auto emit = [&]() {
+        if (active) {
+            OT o[EPL];
+#pragma unroll
+            for (int e = 0; e < EPL; ++e) o[e] = (OT)(acc[e] + cmp[e]);
+            st_vec(Y + (int64_t)r * ldy + col, o);
+        }
+        zero(acc);
+        zero(cmp);
+        cur_start = cur_end;
+        ++r;
+        if (r - win.rw == 32) win.load(r, n, pos, lane);
+        true_end = r < n ? win.end_of(r) : INT_MAX;
+        cur_end = r < b.r1 ? true_end : INT_MAX;
+        kahan = (sizeof(AT) == 4) && (true_end - cur_start > kLongRow);
+    };
+
+    for (int32_t pb = b.p0; pb < b.p1; pb += 32) {
+        const int cnt = (b.p1 - pb) < 32 ? (b.p1 - pb) : 32;
+        int32_t c_l = 0;
+        AT v_l = 0;
+        if (lane < cnt) {
+            c_l = ld_stream(crd + pb + lane);
+            v_l = (AT)ld_stream(vals + pb + lane);
+        }
+        for (int j0 = 0; j0 < cnt; j0 += U) {
+            AT xv[U][EPL];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int32_t cj = __shfl_sync(FULL, c_l, (j0 + u) & 31);
+                if (active && j0 + u < cnt) ld_vec<EPL>(X + (int64_t)cj * ldx + col, xv[u]);
+                else zero(xv[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int j = j0 + u;
+                const AT vj = __shfl_sync(FULL, v_l, j & 31);
+                if (j < cnt) {
+                    const int32_t pj = pb + j;
+                    while (cur_end <= pj) emit();
+                    if (kahan) {
+#pragma unroll
+                        for (int e = 0; e < EPL; ++e) comp_add(acc[e], cmp[e], vj * xv[u][e]);
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < EPL; ++e) acc[e] = fma(vj, xv[u][e], acc[e]);
+                    }
+                }
+            }
+        }
+    }
+    while (r < b.r1) emit();  // rows ending after the last nonzero, empty rows included
+
+    if (carry_row) {
+        int32_t start = b.r1 < n ? __ldg(pos + b.r1) : b.p1;
+        if (start < b.p0) start = b.p0;
+        const bool has = b.p1 > start;
+        if (lane == 0 && blockIdx.y == 0) carry_row[c] = has ? b.r1 : -1;
+        if (has && active) {
+#pragma unroll
+            for (int e = 0; e < EPL; ++e) carry_val[c * L + col + e] = (double)acc[e] + (double)cmp[e];
+        }
+    }
+}
+
+// dX(j,l) = A(i,j) * dY(i,l): walk A's rows in the piece, keep the current row of dY in
+// registers and scatter vals[p] * dY(i,:) into row crd[p] of dX with atomic adds.
+template <typename VT, int EPL>
+__global__ void __launch_bounds__(256) spmm_t_warp_kernel(
+    int64_t n, const int32_t *__restrict__ pos, const int32_t *__restrict__ crd, const VT *__restrict__ vals,
+    const VT *__restrict__ dY, int64_t ldy, typename Traits<VT>::out *__restrict__ dX, int64_t ldx, int64_t L,
+    const int32_t *__restrict__ prow, const int32_t *__restrict__ ppos, int64_t npieces, int64_t P) {
+    using AT = typename Traits<VT>::acc;
+    const int lane = threadIdx.x & 31;
+    const int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (c >= (prow ? npieces : P)) return;
+    const int64_t col = (int64_t)blockIdx.y * (32 * EPL) + (int64_t)lane * EPL;
+    const bool active = col < L;
+    const PieceBounds b = prow ? nnz_piece(c, prow, ppos) : row_piece(c, P, n, pos);
+
+    int32_t r = b.r0;
+    RowWindow win;
+    win.load(r, n, pos, lane);
+    int32_t cur_end = r < n ? win.end_of(r) : INT_MAX;
+    int32_t loaded = -1;  // row of dY held in dy
+    AT dy[EPL];
+    zero(dy);
+    for (int32_t pb = b.p0; pb < b.p1; pb += 32) {
+        const int cnt = (b.p1 - pb) < 32 ? (b.p1 - pb) : 32;
+        int32_t c_l = 0;
+        AT v_l = 0;
+        if (lane < cnt) {
+            c_l = ld_stream(crd + pb + lane);
+            v_l = (AT)ld_stream(vals + pb + lane);
+        }
+        for (int j = 0; j < cnt; ++j) {
+            const int32_t pj = pb + j;
+            while (cur_end <= pj) {
+                ++r;
+                if (r - win.rw == 32) win.load(r, n, pos, lane);
+                cur_end = r < n ? win.end_of(r) : INT_MAX;
+            }
+            if (loaded != r) {
+                if (active) ld_vec<EPL>(dY + (int64_t)r * ldy + col, dy);
+                loaded = r;
+            }
+            const int32_t cj = __shfl_sync(FULL, c_l, j);
+            const AT vj = __shfl_sync(FULL, v_l, j);
+            if (active) {
+                auto *dst = dX + (int64_t)cj * ldx + col;
+                if constexpr (sizeof(AT) == 4 && EPL % 4 == 0) {
+#pragma unroll
+                    for (int q = 0; q < EPL / 4; ++q)
+                        atomicAdd(reinterpret_cast<float4 *>(dst) + q,
+                                  make_float4(vj * dy[4 * q], vj * dy[4 * q + 1], vj * dy[4 * q + 2], vj * dy[4 * q + 3]));
+                } else if constexpr (sizeof(AT) == 4 && EPL == 2) {
+                    atomicAdd(reinterpret_cast<float2 *>(dst), make_float2(vj * dy[0], vj * dy[1]));
+                } else {
+#pragma unroll
+                    for (int e = 0; e < EPL; ++e) atomicAdd(dst + e, vj * dy[e]);
+                }
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ host side
+
+static int64_t default_row_pieces(int64_t n, int64_t nnz, int64_t unit) {
+    int64_t P = ceil_div(n + nnz, unit);
+    return P < 1 ? 1 : P;
+}
+
+template <typename VT, int EPL>
+static spd_status launch_spmm_epl(const spd_csr *A, const void *X, int64_t L, int64_t ldx, void *Y, int64_t ldy,
+                                  int split, const Tuning &tn, void *ws, cudaStream_t st) {
+    using OT = typename Traits<VT>::out;
+    constexpr int U = sizeof(VT) == 8 ? 4 : 8;
+    const int wpb = tn.block_threads / 32;
+    const int64_t ctiles = ceil_div(L, 32 * EPL);
+    const VT *v = static_cast<const VT *>(A->vals);
+    const VT *x = static_cast<const VT *>(X);
+    OT *y = static_cast<OT *>(Y);
+    if (split == SPD_SPLIT_ROW) {
+        const int64_t P = tn.row_pieces > 0 ? tn.row_pieces : default_row_pieces(A->nrows, A->nnz, tn.unit_items);
+        dim3 grid((unsigned)ceil_div(P, wpb), (unsigned)ctiles);
+        spmm_warp_kernel<VT, EPL, U><<<grid, tn.block_threads, 0, st>>>(A->nrows, A->pos, A->crd, v, x, ldx, y, ldy, L,
+                                                                        nullptr, nullptr, 0, P, nullptr, nullptr);
+        return check_launch("spmm_warp_kernel(row)");
+    }
+    WsLayout Lw = layout_warp(A->nrows, A->nnz, split, tn.unit_items, L, true);
+    char *w = static_cast<char *>(ws);
+    int32_t *prow = reinterpret_cast<int32_t *>(w + Lw.part_row);
+    int32_t *ppos = reinterpret_cast<int32_t *>(w + Lw.part_pos);
+    int32_t *crow = reinterpret_cast<int32_t *>(w + Lw.carry_row);
+    double *cval = reinterpret_cast<double *>(w + Lw.carry_val);
+    spd_status s = launch_merge_partition(A->nrows, A->nnz, A->pos, tn.unit_items, Lw.npieces, prow, ppos, st);
+    if (s) return s;
+    dim3 grid((unsigned)ceil_div(Lw.npieces, wpb), (unsigned)ctiles);
+    spmm_warp_kernel<VT, EPL, U><<<grid, tn.block_threads, 0, st>>>(A->nrows, A->pos, A->crd, v, x, ldx, y, ldy, L,
+                                                                    prow, ppos, Lw.npieces, 0, crow, cval);
+    if ((s = check_launch("spmm_warp_kernel(nnz)"))) return s;
+    return launch_carry_fixup<OT>(Lw.npieces, L, crow, cval, y, ldy, st);
+}
+
+template <typename VT>
+static spd_status launch_spmm(const spd_csr *A, const void *X, int64_t L, int64_t ldx, void *Y, int64_t ldy,
+                              int split, const Tuning &tn, void *ws, cudaStream_t st) {
+    using OT = typename Traits<VT>::out;
+    int epl = pick_epl(L, sizeof(VT), sizeof(OT), X, ldx, Y, ldy);
+    switch (epl) {
+        case 1: return launch_spmm_epl<VT, 1>(A, X, L, ldx, Y, ldy, split, tn, ws, st);
+        case 2: return launch_spmm_epl<VT, 2>(A, X, L, ldx, Y, ldy, split, tn, ws, st);
+        case 4: return launch_spmm_epl<VT, 4>(A, X, L, ldx, Y, ldy, split, tn, ws, st);
+        default:
+            if constexpr (sizeof(VT) <= 4) return launch_spmm_epl<VT, 8>(A, X, L, ldx, Y, ldy, split, tn, ws, st);
+            return launch_spmm_epl<VT, 4>(A, X, L, ldx, Y, ldy, split, tn, ws, st);
+    }
+}
+
+template <typename VT, int EPL>
+static spd_status launch_spmm_t_epl(const spd_csr *A, const void *dY, int64_t L, int64_t ldy, void *dX, int64_t ldx,
+                                    int split, const Tuning &tn, void *ws, cudaStream_t st) {
+    using OT = typename Traits<VT>::out;
+    const int wpb = tn.block_threads / 32;
+    const int64_t ctiles = ceil_div(L, 32 * EPL);
+    const VT *v = static_cast<const VT *>(A->vals);
+    const VT *g = static_cast<const VT *>(dY);
+    OT *d = static_cast<OT *>(dX);
+    {
+        spd_status s = launch_zero_rows<OT>(A->ncols, L, d, ldx, st);
+        if (s) return s;
+    }
+    if (A->nrows == 0 || A->nnz == 0) return SPD_OK;
+    if (split == SPD_SPLIT_ROW) {
+        const int64_t P = tn.row_pieces > 0 ? tn.row_pieces : default_row_pieces(A->nrows, A->nnz, tn.unit_items);
+        dim3 grid((unsigned)ceil_div(P, wpb), (unsigned)ctiles);
+        spmm_t_warp_kernel<VT, EPL><<<grid, tn.block_threads, 0, st>>>(A->nrows, A->pos, A->crd, v, g, ldy, d, ldx, L,
+                                                                       nullptr, nullptr, 0, P);
+        return check_launch("spmm_t_warp_kernel(row)");
+    }
+    WsLayout Lw = layout_warp(A->nrows, A->nnz, split, tn.unit_items, L, false);
+    char *w = static_cast<char *>(ws);
+    int32_t *prow = reinterpret_cast<int32_t *>(w + Lw.part_row);
+    int32_t *ppos = reinterpret_cast<int32_t *>(w + Lw.part_pos);
+    spd_status s = launch_merge_partition(A->nrows, A->nnz, A->pos, tn.unit_items, Lw.npieces, prow, ppos, st);
+    if (s) return s;
+    dim3 grid((unsigned)ceil_div(Lw.npieces, wpb), (unsigned)ctiles);
+    spmm_t_warp_kernel<VT, EPL><<<grid, tn.block_threads, 0, st>>>(A->nrows, A->pos, A->crd, v, g, ldy, d, ldx, L,
+                                                                   prow, ppos, Lw.npieces, 0);
+    return check_launch("spmm_t_warp_kernel(nnz)");
+}
+
+template <typename VT>
+static spd_status launch_spmm_t(const spd_csr *A, const void *dY, int64_t L, int64_t ldy, void *dX, int64_t ldx,
+                                int split, const Tuning &tn, void *ws, cudaStream_t st) {
+    using OT = typename Traits<VT>::out;
+    int epl = pick_epl(L, sizeof(VT), sizeof(OT), dY, ldy, dX, ldx);
+    if (sizeof(VT) == 8 && epl > 4) epl = 4;
+    switch (epl) {
+        case 1: return launch_spmm_t_epl<VT, 1>(A, dY, L, ldy, dX, ldx, split, tn, ws, st);
+        case 2: return launch_spmm_t_epl<VT, 2>(A, dY, L, ldy, dX, ldx, split, tn, ws, st);
+        case 4: return launch_spmm_t_epl<VT, 4>(A, dY, L, ldy, dX, ldx, split, tn, ws, st);
+        default:
+            if constexpr (sizeof(VT) <= 4) return launch_spmm_t_epl<VT, 8>(A, dY, L, ldy, dX, ldx, split, tn, ws, st);
+            return launch_spmm_t_epl<VT, 4>(A, dY, L, ldy, dX, ldx, split, tn, ws, st);
+    }
+}
+
+}  // namespace spd
+
+using namespace spd;
+
+extern "C" {
+
+spd_status spd_spmm(const spd_csr *A, const void *X, int64_t L, int64_t ldx, int x_type, void *Y, int64_t ldy,
+                    int y_type, int split, const spd_tune *tune, void *ws, size_t ws_bytes, void *stream) {
+    spd_status s = check_csr(A, true);
+    if (s) return s;
+    if (L < 0) return fail(SPD_ERR_SHAPE, "L %lld < 0", (long long)L);
+    if (x_type != A->vtype) return fail(SPD_ERR_DTYPE, "X type %d differs from the value type %d", x_type, A->vtype);
+    if (y_type != result_type(A->vtype)) return fail(SPD_ERR_DTYPE, "Y type %d; expected %d", y_type, result_type(A->vtype));
+    if ((s = check_dense("X", X, A->ncols, L, ldx, x_type))) return s;
+    if ((s = check_dense("Y", Y, A->nrows, L, ldy, y_type))) return s;
+    Tuning tn;
+    if ((s = read_tune(tune, &tn))) return s;
+    split = resolve_split(split);
+    if (split != SPD_SPLIT_ROW && split != SPD_SPLIT_NNZ) return fail(SPD_ERR_ARG, "unknown split %d", split);
+    WsLayout Lw = layout_warp(A->nrows, A->nnz, split, tn.unit_items, L, true);
+    if ((s = check_ws(Lw, ws, ws_bytes))) return s;
+    if (A->nrows == 0 || L == 0) return SPD_OK;
+    cudaStream_t st = as_stream(stream);
+    switch (A->vtype) {
+        case SPD_F64: return launch_spmm<double>(A, X, L, ldx, Y, ldy, split, tn, ws, st);
+        case SPD_F32: return launch_spmm<float>(A, X, L, ldx, Y, ldy, split, tn, ws, st);
+        case SPD_BF16: return launch_spmm<__nv_bfloat16>(A, X, L, ldx, Y, ldy, split, tn, ws, st);
+        default: return fail(SPD_ERR_DTYPE, "unknown value type %d", A->vtype);
+    }
+}
+
+spd_status spd_spmm_t(const spd_csr *A, const void *dY, int64_t L, int64_t ldy, int dy_type, void *dX, int64_t ldx,
+                      int dx_type, int split, const spd_tune *tune, void *ws, size_t ws_bytes, void *stream) {
+    spd_status s = check_csr(A, true);
+    if (s) return s;
+    if (L < 0) return fail(SPD_ERR_SHAPE, "L %lld < 0", (long long)L);
+    if (dy_type != A->vtype) return fail(SPD_ERR_DTYPE, "dY type %d differs from the value type %d", dy_type, A->vtype);
+    if (dx_type != result_type(A->vtype)) return fail(SPD_ERR_DTYPE, "dX type %d; expected %d", dx_type, result_type(A->vtype));
+    if ((s = check_dense("dY", dY, A->nrows, L, ldy, dy_type))) return s;
+    if ((s = check_dense("dX", dX, A->ncols, L, ldx, dx_type))) return s;
+    Tuning tn;
+    if ((s = read_tune(tune, &tn))) return s;
+    split = resolve_split(split);
+    if (split != SPD_SPLIT_ROW && split != SPD_SPLIT_NNZ) return fail(SPD_ERR_ARG, "unknown split %d", split);
+    WsLayout Lw = layout_warp(A->nrows, A->nnz, split, tn.unit_items, L, false);
+    if ((s = check_ws(Lw, ws, ws_bytes))) return s;
+    if (L == 0) return SPD_OK;
+    cudaStream_t st = as_stream(stream);
+    switch (A->vtype) {
+        case SPD_F64: return launch_spmm_t<double>(A, dY, L, ldy, dX, ldx, split, tn, ws, st);
+        case SPD_F32: return launch_spmm_t<float>(A, dY, L, ldy, dX, ldx, split, tn, ws, st);
+        case SPD_BF16: return launch_spmm_t<__nv_bfloat16>(A, dY, L, ldy, dX, ldx, split, tn, ws, st);
+        default: return fail(SPD_ERR_DTYPE, "unknown value type %d", A->vtype);
+    }
+}
+
+}  // extern "C"

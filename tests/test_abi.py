@@ -1,0 +1,103 @@
+"""C-ABI checks that need no GPU: the library builds, loads, exports every function
+that include/spd.h declares, and rejects bad arguments on the host before any launch."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2207_13901_gb300 import _abi
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", h)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(spd_[a-z0-9_]+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_function():
+    lib = _abi.load()
+    names = header_functions()
+    assert len(names) >= 14
+    for name in names:
+        assert hasattr(lib, name), name
+    # the Python binding declares exactly the functions of the headers
+    assert sorted(_abi.SIGNATURES) == names
+
+
+def test_status_strings_and_version():
+    lib = _abi.load()
+    assert lib.spd_abi_version() == 1
+    for s in range(11):
+        assert lib.spd_status_str(s)
+    assert lib.spd_status_str(99) == b"unknown status"
+
+
+def _csr(nrows=4, ncols=5, nnz=6, vtype=_abi.SPD_F32):
+    # fake, never dereferenced: every check below fails on the host first
+    return _abi.spd_csr(nrows, ncols, nnz, 256, 512, 1024, vtype, 0)
+
+
+def test_host_side_argument_errors():
+    lib = _abi.load()
+    size = ctypes.c_size_t(0)
+    A = _csr()
+    # NULL descriptor / output pointer
+    assert lib.spd_spmv(None, None, 0, None, 0, 0, None, None, 0, None) == 1
+    assert lib.spd_csr_workspace_size(0, ctypes.byref(A), 1, 0, None, None) == 1
+    # negative sizes, inconsistent sizes
+    bad = _csr(nrows=-1)
+    assert lib.spd_csr_workspace_size(0, ctypes.byref(bad), 1, 0, None, ctypes.byref(size)) == 2
+    bad = _csr(nrows=0, nnz=3)
+    assert lib.spd_csr_workspace_size(0, ctypes.byref(bad), 1, 0, None, ctypes.byref(size)) == 2
+    # element type combinations
+    assert lib.spd_spmv(ctypes.byref(A), 4096, _abi.SPD_F64, 8192, _abi.SPD_F32, 1, None, None, 0, None) == 3
+    assert lib.spd_spmv(ctypes.byref(A), 4096, _abi.SPD_F32, 8192, _abi.SPD_F64, 1, None, None, 0, None) == 3
+    assert b"type" in lib.spd_last_error()
+    # misaligned values
+    mis = _abi.spd_csr(4, 5, 6, 256, 512, 1026, _abi.SPD_F32, 0)
+    assert lib.spd_spmv(ctypes.byref(mis), 4096, 1, 8192, 1, 1, None, None, 0, None) == 4
+    # unknown split, bad tuning
+    assert lib.spd_spmv(ctypes.byref(A), 4096, 1, 8192, 1, 7, None, None, 0, None) == 10
+    t = _abi.spd_tune(33, 0, 0, 0)
+    assert lib.spd_spmm(ctypes.byref(A), 4096, 8, 8, 1, 8192, 8, 1, 1, ctypes.byref(t), None, 0, None) == 10
+    # missing or short workspace for the nnz split
+    assert lib.spd_spmv(ctypes.byref(A), 4096, 1, 8192, 1, 1, None, None, 0, None) == 6
+    assert lib.spd_spmm(ctypes.byref(A), 4096, 8, 4, 1, 8192, 8, 1, 1, None, None, 0, None) == 2  # ldx < L
+
+
+def test_workspace_sizes():
+    lib = _abi.load()
+    size = ctypes.c_size_t(0)
+    A = _csr(nrows=1000, ncols=1000, nnz=20000)
+    assert lib.spd_csr_workspace_size(_abi.SPD_OP_SPMV, ctypes.byref(A), _abi.SPD_SPLIT_ROW, 0, None, ctypes.byref(size)) == 0
+    assert size.value == 0  # the row split needs no scratch
+    assert lib.spd_csr_workspace_size(_abi.SPD_OP_SPMV, ctypes.byref(A), _abi.SPD_SPLIT_NNZ, 0, None, ctypes.byref(size)) == 0
+    pieces = -(-21000 // 2048)
+    assert size.value >= 2 * 4 * (pieces + 1) + pieces * (4 + 8)
+    assert lib.spd_csr_workspace_size(_abi.SPD_OP_SPMM, ctypes.byref(A), _abi.SPD_SPLIT_NNZ, 128, None, ctypes.byref(size)) == 0
+    assert size.value >= pieces * 128 * 8  # binary64 carries, one row per piece
+    t = _abi.spd_tune(512, 0, 0, 0)
+    assert lib.spd_csr_workspace_size(_abi.SPD_OP_SDDMM, ctypes.byref(A), _abi.SPD_SPLIT_NNZ, 64, ctypes.byref(t), ctypes.byref(size)) == 0
+    assert size.value >= 2 * 4 * (-(-21000 // 512) + 1)
+    assert lib.spd_csr_workspace_size(_abi.SPD_OP_SPTTV, ctypes.byref(A), 1, 0, None, ctypes.byref(size)) == 10
+    B = _abi.spd_csf3(8, 8, 8, 20, 100, 256, 512, 768, 1024, 2048, _abi.SPD_F32, 0)
+    assert lib.spd_csf3_workspace_size(_abi.SPD_OP_SPMTTKRP, ctypes.byref(B), 1, 32, None, ctypes.byref(size)) == 0
+    assert size.value > 0
+
+
+def test_product_path_has_no_oracle_dependency():
+    """The package never imports or loads the oracle (no CPU fallback)."""
+    pkg = os.path.join(ROOT, "paper_2207_13901_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in text and "from oracle" not in text and "spd_oracle" not in text, f
