@@ -226,6 +226,26 @@ spd_status spd_spmttkrp(const spd_csf3 *B, const void *C, int64_t ldc, const voi
                         int64_t R, int factor_type, void *A, int64_t lda, int a_type, int split,
                         const spd_tune *tune, void *ws, size_t ws_bytes, void *stream);
 
+/* SpMV y(i) = A(i,j) * x(j) for callers that cannot allocate device memory. The paper
+ * has no counterpart: this is a calling convention of this library, not a step of the
+ * method. Callers such as a plugin inside a host framework that owns all device memory,
+ * or a latency-critical path that may not call an allocator, cannot provide the
+ * workspace spd_spmv asks for. This entry runs the same nnz-split SpMV (default tuning)
+ * on a fixed scratch array compiled into the library: 1 MiB of device memory that every
+ * GPU loading the library holds until the process exits. It calls no allocator.
+ *   - Limit: the scratch must hold what spd_csr_workspace_size(SPD_OP_SPMV, A,
+ *     SPD_SPLIT_NNZ, ...) reports, about 20 bytes per 2048 items, so nrows + nnz up to
+ *     about 107 million fits; larger inputs return SPD_ERR_SHAPE before any launch.
+ *   - The first call on a device looks up the array's device address with
+ *     cudaGetSymbolAddress (with that device current) and caches it; make that first
+ *     call before any stream capture.
+ *   - All calls share the one array, which keeps the last call's contents. Each call
+ *     writes every scratch byte before reading it, so no clearing is needed, but calls
+ *     whose GPU work overlaps (different streams, or different threads) race on the
+ *     array: order them on one stream or synchronise between them.
+ *   - Arguments, types, ownership and errors are those of spd_spmv. */
+spd_status spd_spmv_noalloc(const spd_csr *A, const void *x, int x_type, void *y, int y_type, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -13,6 +13,7 @@ import threading
 from . import build as _build
 
 SPD_OK = 0
+SPD_ERR_SHAPE = 2
 SPD_F64, SPD_F32, SPD_BF16 = 0, 1, 2
 SPD_SPLIT_ROW, SPD_SPLIT_NNZ, SPD_SPLIT_AUTO = 0, 1, 2
 SPD_OP_SPMV, SPD_OP_SPMM, SPD_OP_SPMM_T, SPD_OP_SDDMM, SPD_OP_SPTTV, SPD_OP_SPMTTKRP = range(6)
@@ -73,6 +74,7 @@ SIGNATURES = {
     "spd_sddmm": (_I, [_CSR, _P, _I64, _I64, _P, _I64, _I, _P, _I, _I, _TUNE, _P, _SZ, _P]),
     "spd_spttv": (_I, [_CSF, _P, _I, _P, _I, _I, _TUNE, _P, _SZ, _P]),
     "spd_spmttkrp": (_I, [_CSF, _P, _I64, _P, _I64, _I64, _I, _P, _I64, _I, _I, _TUNE, _P, _SZ, _P]),
+    "spd_spmv_noalloc": (_I, [_CSR, _P, _I, _P, _I, _P]),
 }
 
 _lock = threading.Lock()

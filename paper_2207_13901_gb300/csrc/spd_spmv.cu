@@ -249,6 +249,15 @@ static spd_status dispatch_spmv(int vtype, int64_t n, int64_t nnz, const int32_t
     }
 }
 
+// Nnz-split SpMV with default tuning on a scratch area the caller already owns (laid out
+// as layout_spmv describes); used by the entry point that allocates nothing.
+spd_status spmv_nnz_on_scratch(const spd_csr *A, const void *x, void *y, void *scratch, cudaStream_t st) {
+    Tuning tn;
+    read_tune(nullptr, &tn);
+    return dispatch_spmv(A->vtype, A->nrows, A->nnz, A->pos, A->crd, A->vals, x, y, SPD_SPLIT_NNZ, tn, 0, nullptr,
+                         scratch, st);
+}
+
 }  // namespace spd
 
 using namespace spd;
