@@ -123,12 +123,14 @@ typedef struct {
  *                 must be a multiple of 32 in [32, 65536].
  *   row_pieces    number of pieces P of SPD_SPLIT_ROW (1 <= P <= 2^31-1).
  *   block_threads threads per block for the warp-per-unit kernels: 64..1024,
- *                 multiple of 32. */
+ *                 multiple of 32.
+ *   inflight      dense rows a warp keeps in flight per group in SpMM (4 or 8;
+ *                 binary64 always uses 4). */
 typedef struct {
     int32_t unit_items;
     int32_t row_pieces;
     int32_t block_threads;
-    int32_t reserved;
+    int32_t inflight;
 } spd_tune;
 
 /* -------------------------------------------------------------------- misc */

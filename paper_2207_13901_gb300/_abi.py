@@ -46,7 +46,7 @@ class spd_csf3(ctypes.Structure):
 class spd_tune(ctypes.Structure):
     _fields_ = [
         ("unit_items", ctypes.c_int32), ("row_pieces", ctypes.c_int32),
-        ("block_threads", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("block_threads", ctypes.c_int32), ("inflight", ctypes.c_int32),
     ]
 
 

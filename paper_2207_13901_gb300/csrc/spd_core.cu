@@ -64,6 +64,7 @@ spd_status read_tune(const spd_tune *t, Tuning *out) {
     out->unit_items = kWarpUnitDefault;
     out->row_pieces = 0;
     out->block_threads = kWarpBlockDefault;
+    out->inflight = 8;
     if (!t) return SPD_OK;
     if (t->unit_items) {
         if (t->unit_items < 32 || t->unit_items > 65536 || t->unit_items % 32)
@@ -78,6 +79,10 @@ spd_status read_tune(const spd_tune *t, Tuning *out) {
         if (t->block_threads < 64 || t->block_threads > 1024 || t->block_threads % 32)
             return fail(SPD_ERR_ARG, "block_threads %d not a multiple of 32 in [64, 1024]", t->block_threads);
         out->block_threads = t->block_threads;
+    }
+    if (t->inflight) {
+        if (t->inflight != 4 && t->inflight != 8) return fail(SPD_ERR_ARG, "inflight %d is not 4 or 8", t->inflight);
+        out->inflight = t->inflight;
     }
     return SPD_OK;
 }

@@ -132,6 +132,16 @@ __device__ __forceinline__ void st_vec(double *p, const double (&v)[N]) {
     }
 }
 
+// Kahan's compensated accumulation of a product a*b: s carries the running sum and c the
+// negated rounding error of the additions so far (s - c approximates the exact sum).
+template <typename T>
+__device__ __forceinline__ void kahan_fma(T &s, T &c, T a, T b) {
+    const T y = fma(a, b, -c);
+    const T t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
 // Compensated accumulation (Neumaier's variant of Kahan summation): hi + lo carries
 // the running sum; lo collects the rounding error of every addition.
 template <typename T>
@@ -201,6 +211,7 @@ struct Tuning {
     int64_t unit_items;   // warp-unit size of SPD_SPLIT_NNZ (warp kernels)
     int64_t row_pieces;   // P of SPD_SPLIT_ROW (0 = per-kernel default)
     int block_threads;    // threads per block (warp kernels)
+    int inflight;         // dense rows in flight per group (SpMM)
 };
 spd_status read_tune(const spd_tune *t, Tuning *out);
 int resolve_split(int split);

@@ -6,8 +6,8 @@
 // (a 16- or 32-byte vector per lane). crd/vals are streamed 32 at a time and broadcast
 // with shuffles; U rows of X are in flight before they are consumed. Row ends come
 // from a 32-entry window of pos held one entry per lane. A row is written once, when
-// its end item is reached; rows longer than 4096 nonzeros accumulate with compensated
-// (Kahan-Neumaier) summation in the binary32 modes. In the nnz split the partial row
+// its end item is reached; rows longer than 4096 nonzeros accumulate with Kahan's
+// compensated summation in the binary32 modes. In the nnz split the partial row
 // at a piece end is stored as binary64 and added by a fix-up kernel.
 #include "spd_internal.cuh"
 
@@ -35,10 +35,10 @@ struct RowWindow {
     __device__ __forceinline__ int32_t end_of(int32_t r) const { return __shfl_sync(FULL, true_end, r - rw); }
 };
 
-template <typename VT, int EPL, int U>
+template <typename VT, int EPL, int U, bool FULLTILE>
 __global__ void __launch_bounds__(256) spmm_warp_kernel(
     int64_t n, const int32_t *__restrict__ pos, const int32_t *__restrict__ crd, const VT *__restrict__ vals,
-    const VT *__restrict__ X, int64_t ldx, typename Traits<VT>::out *__restrict__ Y, int64_t ldy, int64_t L,
+    const VT *__restrict__ X, uint32_t ldx_bytes, typename Traits<VT>::out *__restrict__ Y, int64_t ldy, int64_t L,
     const int32_t *__restrict__ prow, const int32_t *__restrict__ ppos, int64_t npieces, int64_t P,
     int32_t *__restrict__ carry_row, double *__restrict__ carry_val) {
     using AT = typename Traits<VT>::acc;
@@ -47,8 +47,12 @@ __global__ void __launch_bounds__(256) spmm_warp_kernel(
     const int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (c >= (prow ? npieces : P)) return;  // whole warp
     const int64_t col = (int64_t)blockIdx.y * (32 * EPL) + (int64_t)lane * EPL;
-    const bool active = col < L;
+    const bool active = FULLTILE || col < L;
     const PieceBounds b = prow ? nnz_piece(c, prow, ppos) : row_piece(c, P, n, pos);
+    // this lane's columns of row 0 of X; row j starts j * ldx_bytes further (one wide
+    // multiply-add per gathered row)
+    const char *__restrict__ Xc = reinterpret_cast<const char *>(X + col);
+    auto xrow = [&](int32_t j) { return reinterpret_cast<const VT *>(Xc + (uint64_t)(uint32_t)j * ldx_bytes); };
 
     AT acc[EPL], cmp[EPL];
     zero(acc);
@@ -65,7 +69,7 @@ __global__ void __launch_bounds__(256) spmm_warp_kernel(
         if (active) {
             OT o[EPL];
 #pragma unroll
-            for (int e = 0; e < EPL; ++e) o[e] = (OT)(acc[e] + cmp[e]);
+            for (int e = 0; e < EPL; ++e) o[e] = (OT)(acc[e] - cmp[e]);
             st_vec(Y + (int64_t)r * ldy + col, o);
         }
         zero(acc);
@@ -78,39 +82,90 @@ __global__ void __launch_bounds__(256) spmm_warp_kernel(
         kahan = (sizeof(AT) == 4) && (true_end - cur_start > kLongRow);
     };
 
-    for (int32_t pb = b.p0; pb < b.p1; pb += 32) {
-        const int cnt = (b.p1 - pb) < 32 ? (b.p1 - pb) : 32;
-        int32_t c_l = 0;
-        AT v_l = 0;
-        if (lane < cnt) {
-            c_l = ld_stream(crd + pb + lane);
-            v_l = (AT)ld_stream(vals + pb + lane);
-        }
+    // The piece's nonzeros are streamed in windows of 32: each lane loads one crd/vals
+    // pair of the next window while the current window is consumed from this warp's
+    // shared-memory slots, four entries per broadcast read. Entries are consumed in
+    // groups of U whose rows of X are loaded back to back. A group inside the current row
+    // (the common case) takes the fast path: U broadcast-multiply-adds, no checks. The
+    // loops stay rolled so that the kernel fits the instruction cache.
+    extern __shared__ __align__(16) unsigned char spmm_smem[];
+    const int wid = threadIdx.x >> 5;
+    int32_t *s_crd = reinterpret_cast<int32_t *>(spmm_smem) + wid * 64;  // [2][32]
+    AT *s_val = reinterpret_cast<AT *>(spmm_smem + (blockDim.x >> 5) * 64 * sizeof(int32_t)) + wid * 64;
+    int32_t pb = b.p0;
+    int cnt = (b.p1 - pb) < 32 ? (b.p1 - pb) : 32;
+    int buf = 0;
+    s_crd[lane] = lane < cnt ? ld_stream(crd + pb + lane) : 0;
+    s_val[lane] = lane < cnt ? (AT)ld_stream(vals + pb + lane) : (AT)0;
+    __syncwarp();
+    while (pb < b.p1) {
+        const int32_t pn = pb + 32;
+        const int cnt_n = b.p1 - pn <= 0 ? 0 : (b.p1 - pn < 32 ? b.p1 - pn : 32);
+        const int32_t c_n = lane < cnt_n ? ld_stream(crd + pn + lane) : 0;
+        const AT v_n = lane < cnt_n ? (AT)ld_stream(vals + pn + lane) : (AT)0;
+        const int32_t *wc = s_crd + buf * 32;
+        const AT *wv = s_val + buf * 32;
+#pragma unroll 1
         for (int j0 = 0; j0 < cnt; j0 += U) {
             AT xv[U][EPL];
+            int32_t cj[U];
+            AT vj[U];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int32_t cj = __shfl_sync(FULL, c_l, (j0 + u) & 31);
-                if (active && j0 + u < cnt) ld_vec<EPL>(X + (int64_t)cj * ldx + col, xv[u]);
-                else zero(xv[u]);
+            for (int q = 0; q < U / 4; ++q) {
+                const int4 c4 = *reinterpret_cast<const int4 *>(wc + j0 + 4 * q);
+                cj[4 * q] = c4.x; cj[4 * q + 1] = c4.y; cj[4 * q + 2] = c4.z; cj[4 * q + 3] = c4.w;
             }
+            const int gcnt = cnt - j0 < U ? cnt - j0 : U;  // valid entries of this group
+            if (active && gcnt == U) {
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int j = j0 + u;
-                const AT vj = __shfl_sync(FULL, v_l, j & 31);
-                if (j < cnt) {
-                    const int32_t pj = pb + j;
-                    while (cur_end <= pj) emit();
-                    if (kahan) {
+                for (int u = 0; u < U; ++u) ld_vec<EPL>(xrow(cj[u]), xv[u]);
+            } else {
 #pragma unroll
-                        for (int e = 0; e < EPL; ++e) comp_add(acc[e], cmp[e], vj * xv[u][e]);
-                    } else {
-#pragma unroll
-                        for (int e = 0; e < EPL; ++e) acc[e] = fma(vj, xv[u][e], acc[e]);
-                    }
+                for (int u = 0; u < U; ++u) {
+                    if (active && u < gcnt) ld_vec<EPL>(xrow(cj[u]), xv[u]);
+                    else zero(xv[u]);
                 }
             }
+#pragma unroll
+            for (int u = 0; u < U; ++u) vj[u] = wv[j0 + u];
+            if (!kahan && gcnt == U && (int64_t)pb + j0 + U <= (int64_t)cur_end) {
+                // fast path: the whole group lies inside the current row
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+#pragma unroll
+                    for (int e = 0; e < EPL; ++e) acc[e] = fma(vj[u], xv[u][e], acc[e]);
+                }
+                continue;
+            }
+            // general path: consume the group one row segment at a time; rows (empty ones
+            // included) that end before the next entry are written at the one emit site
+            int lo = 0;
+            while (lo < gcnt) {
+                while (cur_end <= pb + j0 + lo) emit();
+                const int64_t in_row = (int64_t)cur_end - (pb + j0);
+                const int hi = in_row < gcnt ? (int)in_row : gcnt;
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    if (u >= lo && u < hi) {
+                        if (kahan) {
+#pragma unroll
+                            for (int e = 0; e < EPL; ++e) kahan_fma(acc[e], cmp[e], vj[u], xv[u][e]);
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < EPL; ++e) acc[e] = fma(vj[u], xv[u][e], acc[e]);
+                        }
+                    }
+                }
+                lo = hi;
+            }
         }
+        buf ^= 1;
+        __syncwarp();
+        s_crd[buf * 32 + lane] = c_n;
+        s_val[buf * 32 + lane] = v_n;
+        __syncwarp();
+        pb = pn;
+        cnt = cnt_n;
     }
     while (r < b.r1) emit();  // rows ending after the last nonzero, empty rows included
 
@@ -121,7 +176,7 @@ __global__ void __launch_bounds__(256) spmm_warp_kernel(
         if (lane == 0 && blockIdx.y == 0) carry_row[c] = has ? b.r1 : -1;
         if (has && active) {
 #pragma unroll
-            for (int e = 0; e < EPL; ++e) carry_val[c * L + col + e] = (double)acc[e] + (double)cmp[e];
+            for (int e = 0; e < EPL; ++e) carry_val[c * L + col + e] = (double)acc[e] - (double)cmp[e];
         }
     }
 }
@@ -194,21 +249,23 @@ static int64_t default_row_pieces(int64_t n, int64_t nnz, int64_t unit) {
     return P < 1 ? 1 : P;
 }
 
-template <typename VT, int EPL>
+template <typename VT, int EPL, int U, bool FULLTILE>
 static spd_status launch_spmm_epl(const spd_csr *A, const void *X, int64_t L, int64_t ldx, void *Y, int64_t ldy,
                                   int split, const Tuning &tn, void *ws, cudaStream_t st) {
     using OT = typename Traits<VT>::out;
-    constexpr int U = sizeof(VT) == 8 ? 4 : 8;
+    using AT = typename Traits<VT>::acc;
     const int wpb = tn.block_threads / 32;
     const int64_t ctiles = ceil_div(L, 32 * EPL);
+    const size_t smem = (size_t)wpb * 64 * (sizeof(int32_t) + sizeof(AT));  // two windows per warp
     const VT *v = static_cast<const VT *>(A->vals);
     const VT *x = static_cast<const VT *>(X);
     OT *y = static_cast<OT *>(Y);
     if (split == SPD_SPLIT_ROW) {
         const int64_t P = tn.row_pieces > 0 ? tn.row_pieces : default_row_pieces(A->nrows, A->nnz, tn.unit_items);
         dim3 grid((unsigned)ceil_div(P, wpb), (unsigned)ctiles);
-        spmm_warp_kernel<VT, EPL, U><<<grid, tn.block_threads, 0, st>>>(A->nrows, A->pos, A->crd, v, x, ldx, y, ldy, L,
-                                                                        nullptr, nullptr, 0, P, nullptr, nullptr);
+        spmm_warp_kernel<VT, EPL, U, FULLTILE><<<grid, tn.block_threads, smem, st>>>(
+            A->nrows, A->pos, A->crd, v, x, (uint32_t)(ldx * sizeof(VT)), y, ldy, L, nullptr, nullptr, 0, P, nullptr,
+            nullptr);
         return check_launch("spmm_warp_kernel(row)");
     }
     WsLayout Lw = layout_warp(A->nrows, A->nnz, split, tn.unit_items, L, true);
@@ -220,10 +277,29 @@ static spd_status launch_spmm_epl(const spd_csr *A, const void *X, int64_t L, in
     spd_status s = launch_merge_partition(A->nrows, A->nnz, A->pos, tn.unit_items, Lw.npieces, prow, ppos, st);
     if (s) return s;
     dim3 grid((unsigned)ceil_div(Lw.npieces, wpb), (unsigned)ctiles);
-    spmm_warp_kernel<VT, EPL, U><<<grid, tn.block_threads, 0, st>>>(A->nrows, A->pos, A->crd, v, x, ldx, y, ldy, L,
-                                                                    prow, ppos, Lw.npieces, 0, crow, cval);
+    spmm_warp_kernel<VT, EPL, U, FULLTILE><<<grid, tn.block_threads, smem, st>>>(
+        A->nrows, A->pos, A->crd, v, x, (uint32_t)(ldx * sizeof(VT)), y, ldy, L, prow, ppos, Lw.npieces, 0, crow,
+        cval);
     if ((s = check_launch("spmm_warp_kernel(nnz)"))) return s;
     return launch_carry_fixup<OT>(Lw.npieces, L, crow, cval, y, ldy, st);
+}
+
+template <typename VT, int EPL, bool FULLTILE>
+static spd_status launch_spmm_f(const spd_csr *A, const void *X, int64_t L, int64_t ldx, void *Y, int64_t ldy,
+                                int split, const Tuning &tn, void *ws, cudaStream_t st) {
+    if constexpr (sizeof(VT) == 8) {
+        return launch_spmm_epl<VT, EPL, 4, FULLTILE>(A, X, L, ldx, Y, ldy, split, tn, ws, st);
+    } else {
+        if (tn.inflight == 4) return launch_spmm_epl<VT, EPL, 4, FULLTILE>(A, X, L, ldx, Y, ldy, split, tn, ws, st);
+        return launch_spmm_epl<VT, EPL, 8, FULLTILE>(A, X, L, ldx, Y, ldy, split, tn, ws, st);
+    }
+}
+
+template <typename VT, int EPL>
+static spd_status launch_spmm_u(const spd_csr *A, const void *X, int64_t L, int64_t ldx, void *Y, int64_t ldy,
+                                int split, const Tuning &tn, void *ws, cudaStream_t st) {
+    if (L % (32 * EPL) == 0) return launch_spmm_f<VT, EPL, true>(A, X, L, ldx, Y, ldy, split, tn, ws, st);
+    return launch_spmm_f<VT, EPL, false>(A, X, L, ldx, Y, ldy, split, tn, ws, st);
 }
 
 template <typename VT>
@@ -232,12 +308,12 @@ static spd_status launch_spmm(const spd_csr *A, const void *X, int64_t L, int64_
     using OT = typename Traits<VT>::out;
     int epl = pick_epl(L, sizeof(VT), sizeof(OT), X, ldx, Y, ldy);
     switch (epl) {
-        case 1: return launch_spmm_epl<VT, 1>(A, X, L, ldx, Y, ldy, split, tn, ws, st);
-        case 2: return launch_spmm_epl<VT, 2>(A, X, L, ldx, Y, ldy, split, tn, ws, st);
-        case 4: return launch_spmm_epl<VT, 4>(A, X, L, ldx, Y, ldy, split, tn, ws, st);
+        case 1: return launch_spmm_u<VT, 1>(A, X, L, ldx, Y, ldy, split, tn, ws, st);
+        case 2: return launch_spmm_u<VT, 2>(A, X, L, ldx, Y, ldy, split, tn, ws, st);
+        case 4: return launch_spmm_u<VT, 4>(A, X, L, ldx, Y, ldy, split, tn, ws, st);
         default:
-            if constexpr (sizeof(VT) <= 4) return launch_spmm_epl<VT, 8>(A, X, L, ldx, Y, ldy, split, tn, ws, st);
-            return launch_spmm_epl<VT, 4>(A, X, L, ldx, Y, ldy, split, tn, ws, st);
+            if constexpr (sizeof(VT) <= 4) return launch_spmm_u<VT, 8>(A, X, L, ldx, Y, ldy, split, tn, ws, st);
+            return launch_spmm_u<VT, 4>(A, X, L, ldx, Y, ldy, split, tn, ws, st);
     }
 }
 
@@ -305,6 +381,8 @@ spd_status spd_spmm(const spd_csr *A, const void *X, int64_t L, int64_t ldx, int
     if (y_type != result_type(A->vtype)) return fail(SPD_ERR_DTYPE, "Y type %d; expected %d", y_type, result_type(A->vtype));
     if ((s = check_dense("X", X, A->ncols, L, ldx, x_type))) return s;
     if ((s = check_dense("Y", Y, A->nrows, L, ldy, y_type))) return s;
+    if ((uint64_t)ldx * dtype_size(x_type) >= (uint64_t(1) << 32))
+        return fail(SPD_ERR_SHAPE, "X row stride of %lld elements exceeds 4 GiB", (long long)ldx);
     Tuning tn;
     if ((s = read_tune(tune, &tn))) return s;
     split = resolve_split(split);

@@ -18,19 +18,24 @@
 
 namespace spd {
 
+// Shared-memory index with one padding word per 32 entries: each thread consumes IPT
+// consecutive entries, so without the skew a warp's 32 threads would fall on only
+// 32/IPT banks.
+__device__ __forceinline__ int skew(int i) { return i + (i >> 5); }
+
 // Number of rows q < nr whose end item s_end[q] + q lies before item k.
 __device__ __forceinline__ int merge_count(const int32_t *s_end, int nr, int k) {
     int lo = 0, hi = nr < k ? nr : k;
     while (lo < hi) {
         int mid = (lo + hi) >> 1;
-        if (s_end[mid] + mid < k) lo = mid + 1;
+        if (s_end[skew(mid)] + mid < k) lo = mid + 1;
         else hi = mid;
     }
     return lo;
 }
 
 template <typename VT, int NT, int IPT>
-__global__ void __launch_bounds__(NT) spmv_tile_kernel(
+__global__ void __launch_bounds__(NT, sizeof(VT) == 8 ? 6 : 8) spmv_tile_kernel(
     int64_t n, const int32_t *__restrict__ pos, const int32_t *__restrict__ crd, const VT *__restrict__ vals,
     const VT *__restrict__ x, typename Traits<VT>::out *__restrict__ y,
     const int32_t *__restrict__ prow, const int32_t *__restrict__ ppos,  // nnz split
@@ -41,8 +46,8 @@ __global__ void __launch_bounds__(NT) spmv_tile_kernel(
     constexpr int TILE = NT * IPT;
     constexpr int NW = NT / 32;
     constexpr unsigned FULL = 0xffffffffu;
-    __shared__ int32_t s_end[TILE];
-    __shared__ AT s_prod[TILE];
+    __shared__ int32_t s_end[TILE + TILE / 32];
+    __shared__ AT s_prod[TILE + TILE / 32];
     __shared__ AT s_wv[NW];
     __shared__ int s_wf[NW];
     __shared__ AT s_tv;
@@ -71,7 +76,7 @@ __global__ void __launch_bounds__(NT) spmv_tile_kernel(
         if (rem_rows + rem_nnz == 0) break;
         const int nr = (int)(rem_rows < TILE ? rem_rows : TILE);
         const int items = (int)((rem_rows + rem_nnz) < TILE ? (rem_rows + rem_nnz) : TILE);
-        for (int q = tid; q < nr; q += NT) s_end[q] = ld_stream(pos + r + 1 + q) - p;
+        for (int q = tid; q < nr; q += NT) s_end[skew(q)] = ld_stream(pos + r + 1 + q) - p;
         __syncthreads();
         const int ic = merge_count(s_end, nr, items);
         const int jc = items - ic;
@@ -88,7 +93,7 @@ __global__ void __launch_bounds__(NT) spmv_tile_kernel(
 #pragma unroll
             for (int k = 0; k < IPT; ++k) {
                 int q = tid + k * NT;
-                if (q < jc) s_prod[q] = vv[k] * (AT)ld_gather(x + cc[k]);
+                if (q < jc) s_prod[skew(q)] = vv[k] * (AT)ld_gather(x + cc[k]);
             }
         }
         __syncthreads();
@@ -102,7 +107,7 @@ __global__ void __launch_bounds__(NT) spmv_tile_kernel(
 #pragma unroll
         for (int k = 0; k < IPT; ++k) {
             if (k0 + k < k1) {
-                if (i < nr && s_end[i] <= j) {  // row i ends here: all its children consumed
+                if (i < nr && s_end[skew(i)] <= j) {  // row i ends here: all its children consumed
                     if (first_row < 0) {
                         first_row = i;
                         first_val = acc;
@@ -112,7 +117,7 @@ __global__ void __launch_bounds__(NT) spmv_tile_kernel(
                     acc = 0;
                     ++i;
                 } else {
-                    acc += s_prod[j];
+                    acc += s_prod[skew(j)];
                     ++j;
                 }
             }
