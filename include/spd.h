@@ -228,6 +228,51 @@ spd_status spd_spmttkrp(const spd_csf3 *B, const void *C, int64_t ldc, const voi
                         int64_t R, int factor_type, void *A, int64_t lda, int a_type, int split,
                         const spd_tune *tune, void *ws, size_t ws_bytes, void *stream);
 
+/* -------------------------------------------------------------------- batches */
+
+/* One product Y_m = A_m X_m of a batched SpMM (Section VI-A's SpMM statement, applied
+ * to many independent matrices). X: A.ncols x L (ldx), Y: A.nrows x L (ldy), both of the
+ * batch's value type / result type. split: SPD_SPLIT_ROW or SPD_SPLIT_NNZ for this
+ * matrix; unit_items: items per piece for this matrix (multiple of 32 in [32, 65536];
+ * 0 = the tuning's unit_items). */
+typedef struct {
+    spd_csr A;
+    const void *X;
+    int64_t ldx;
+    void *Y;
+    int64_t ldy;
+    int32_t split;
+    int32_t unit_items;
+} spd_batch_item;
+
+/* Filled by spd_spmm_batched_plan; owned by the caller; read by spd_spmm_batched_run.
+ * It points into the caller's workspace, which must outlive every run of the plan. */
+typedef struct {
+    int64_t count, total_pieces, L;
+    int32_t vtype, epl, block_threads, grid, fulltile, has_nnz;
+    void *ws;
+    size_t off_desc, off_pstart, off_prow, off_ppos, off_crow, off_cval;
+} spd_batch_plan;
+
+/* Workspace bytes of a batch (host only). items: host array of count entries. */
+spd_status spd_spmm_batched_workspace_size(int64_t count, const spd_batch_item *items, int64_t L, int vtype,
+                                           const spd_tune *tune, size_t *bytes);
+
+/* Lays the pieces of every matrix end to end (row split: universe partition of its
+ * rows; nnz split: fused non-zero partition computed here on the device) and writes the
+ * descriptors into ws. Copies from host memory and synchronizes `stream` before
+ * returning. The matrices' structure must not change while the plan is in use (values,
+ * X and Y may). */
+spd_status spd_spmm_batched_plan(int64_t count, const spd_batch_item *items, int64_t L, int vtype,
+                                 const spd_tune *tune, void *ws, size_t ws_bytes, spd_batch_plan *plan,
+                                 void *stream);
+
+/* Runs every product of the plan: one persistent kernel whose warps take the global
+ * pieces in a static stride, then one fix-up kernel for the nnz-split matrices.
+ * Asynchronous; allocates nothing and never synchronizes, so it may be captured in a
+ * CUDA graph and replayed. */
+spd_status spd_spmm_batched_run(const spd_batch_plan *plan, void *stream);
+
 /* SpMV y(i) = A(i,j) * x(j) for callers that cannot allocate device memory. The paper
  * has no counterpart: this is a calling convention of this library, not a step of the
  * method. Callers such as a plugin inside a host framework that owns all device memory,

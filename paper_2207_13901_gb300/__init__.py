@@ -7,7 +7,8 @@ kernels behind the C ABI of include/spd.h. PyTorch supplies memory and streams.
 """
 from .ops import (CSF3, CSR, csf3_workspace_size, csr_workspace_size, partition, result_dtype, sddmm, spmm, spmm_t,
                   spmttkrp, spmv, spttv, validate)
-from . import autograd
+from . import autograd, batched
+from .batched import SpMMBatch
 
 __all__ = ["CSR", "CSF3", "spmv", "spmm", "spmm_t", "sddmm", "spttv", "spmttkrp", "validate", "partition",
-           "csr_workspace_size", "csf3_workspace_size", "result_dtype", "autograd"]
+           "csr_workspace_size", "csf3_workspace_size", "result_dtype", "autograd", "batched", "SpMMBatch"]

@@ -50,6 +50,24 @@ class spd_tune(ctypes.Structure):
     ]
 
 
+class spd_batch_item(ctypes.Structure):
+    _fields_ = [
+        ("A", spd_csr), ("X", ctypes.c_void_p), ("ldx", ctypes.c_int64), ("Y", ctypes.c_void_p),
+        ("ldy", ctypes.c_int64), ("split", ctypes.c_int32), ("unit_items", ctypes.c_int32),
+    ]
+
+
+class spd_batch_plan(ctypes.Structure):
+    _fields_ = [
+        ("count", ctypes.c_int64), ("total_pieces", ctypes.c_int64), ("L", ctypes.c_int64),
+        ("vtype", ctypes.c_int32), ("epl", ctypes.c_int32), ("block_threads", ctypes.c_int32),
+        ("grid", ctypes.c_int32), ("fulltile", ctypes.c_int32), ("has_nnz", ctypes.c_int32),
+        ("ws", ctypes.c_void_p),
+        ("off_desc", ctypes.c_size_t), ("off_pstart", ctypes.c_size_t), ("off_prow", ctypes.c_size_t),
+        ("off_ppos", ctypes.c_size_t), ("off_crow", ctypes.c_size_t), ("off_cval", ctypes.c_size_t),
+    ]
+
+
 _P = ctypes.c_void_p
 _I = ctypes.c_int
 _I64 = ctypes.c_int64
@@ -74,6 +92,11 @@ SIGNATURES = {
     "spd_sddmm": (_I, [_CSR, _P, _I64, _I64, _P, _I64, _I, _P, _I, _I, _TUNE, _P, _SZ, _P]),
     "spd_spttv": (_I, [_CSF, _P, _I, _P, _I, _I, _TUNE, _P, _SZ, _P]),
     "spd_spmttkrp": (_I, [_CSF, _P, _I64, _P, _I64, _I64, _I, _P, _I64, _I, _I, _TUNE, _P, _SZ, _P]),
+    "spd_spmm_batched_workspace_size": (_I, [_I64, ctypes.POINTER(spd_batch_item), _I64, _I, _TUNE,
+                                             ctypes.POINTER(ctypes.c_size_t)]),
+    "spd_spmm_batched_plan": (_I, [_I64, ctypes.POINTER(spd_batch_item), _I64, _I, _TUNE, _P, _SZ,
+                                   ctypes.POINTER(spd_batch_plan), _P]),
+    "spd_spmm_batched_run": (_I, [ctypes.POINTER(spd_batch_plan), _P]),
     "spd_spmv_noalloc": (_I, [_CSR, _P, _I, _P, _I, _P]),
 }
 
