@@ -52,6 +52,8 @@ def parse_args(argv=None):
     p.add_argument("--no-variants", action="store_true", help="skip the per-variant table")
     p.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of CPU oracle work for cpu_baseline")
     p.add_argument("--e2e-steps", type=int, default=5)
+    p.add_argument("--rows", default="all",
+                   help="comma list of extra hot-path rows to measure: cfg1,sddmm,backward,csf,batched (or all, none)")
     return p.parse_args(argv)
 
 
@@ -396,6 +398,24 @@ def run_gpu(args):
     if rank == 0 and ws == 1:
         cpu = cpu_baseline(A, x32, X32, args.cpu_budget)
 
+    rows_out = {}
+    wanted = {"cfg1", "sddmm", "backward", "csf", "batched"} if args.rows == "all" else \
+        (set() if args.rows == "none" else set(args.rows.split(",")))
+    for name, fn in (("cfg1", lambda: row_cfg1(hbm)), ("backward", lambda: row_backward(A, X32, hbm)),
+                     ("sddmm", lambda: row_sddmm(hbm)), ("csf", lambda: row_csf(hbm)),
+                     ("batched", lambda: row_batched(hbm))):
+        if name not in wanted:
+            continue
+        if name == "backward":
+            del Ad, v32, Xd, Y
+            torch.cuda.empty_cache()
+        try:
+            t_row = time.time()
+            rows_out[name] = fn()
+            rows_out[name]["wall_s"] = round(time.time() - t_row, 1)
+        except Exception as exc:  # a failing row is reported, the headline line still prints
+            rows_out[name] = {"failed": "%s: %s" % (type(exc).__name__, exc)}
+
     clk = clocks.summary()
     if rank == 0:
         line = {
@@ -444,11 +464,268 @@ def run_gpu(args):
             "cpu_baseline": cpu,
             "variants": variants,
             "autotune": {"spmm": spmm_table, "spmv": spmv_table},
+            "rows": rows_out,
         }
         print(json.dumps(line))
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- other rows
+
+def _time_ms(fn, reps=5, warm=2):
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def _entry(ms, units, nbytes, hbm, unit_name="nnz"):
+    return {"ms": round(ms, 4), unit_name + "_per_s": units / (ms * 1e-3),
+            "algorithmic_GBps": round(nbytes / (ms * 1e-3) / 1e9, 1), "hbm_frac": round(nbytes / (ms * 1e-3) / 1e9 / hbm, 4)}
+
+
+def _rounded(a, dt):
+    import torch
+    return torch.as_tensor(np.asarray(a)).to(dt).double().numpy()
+
+
+def row_cfg1(hbm):
+    """SpMV on the 4096 x 4096 uniform matrix (16 per row), binary64: latency-bound;
+    timed as a replayed CUDA graph of the call."""
+    import torch
+    import oracle
+    import spd_synth
+    import paper_2207_13901_gb300 as spd
+    A = spd_synth.uniform_csr(4096, 4096, 16, seed=0)
+    x = spd_synth.uniform(4096, seed=2)
+    dA = spd.CSR.from_host(A.pos, A.crd, A.vals, (4096, 4096), dtype=torch.float64)
+    xd = torch.as_tensor(x).cuda()
+    out = {}
+    for split in ("nnz", "row"):
+        y = torch.empty(4096, dtype=torch.float64, device="cuda")
+        ws = torch.empty(max(spd.csr_workspace_size(0, dA, split), 1), dtype=torch.uint8, device="cuda")
+        spd.spmv(dA, xd, y, split=split, ws=ws)
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            spd.spmv(dA, xd, y, split=split, ws=ws)
+        torch.cuda.current_stream().wait_stream(s)
+        with torch.cuda.graph(g):
+            for _ in range(20):
+                spd.spmv(dA, xd, y, split=split, ws=ws)
+        ms = _time_ms(lambda: g.replay(), reps=20) / 20
+        ref = oracle.spmv(A.pos, A.crd, A.vals, x, accurate=True)
+        sc = oracle.spmv(A.pos, A.crd, np.abs(A.vals), np.abs(x))
+        e = _entry(ms, A.nnz, algorithmic_bytes("spmv", 4096, A.nnz, 8, 8, 8), hbm)
+        e["us"] = round(ms * 1e3, 2)
+        e["error"] = error_stats(y.cpu().numpy(), ref, sc)
+        out["spmv_f64_" + split] = e
+    t = time.perf_counter()
+    for _ in range(20):
+        oracle.spmv(A.pos, A.crd, A.vals, x)
+    dt = (time.perf_counter() - t) / 20
+    out["oracle"] = {"nnz_per_s": A.nnz / dt, "cores": 1, "sample": "whole matrix"}
+    return out
+
+
+def row_sddmm(hbm):
+    """SDDMM on the 2^20-row R-MAT (32 samples per row), K in {32, 128, 256}, binary32 and
+    bfloat16, C and D N(0,1); autotuned split/piece size per case."""
+    import torch
+    import oracle
+    import spd_synth
+    import paper_2207_13901_gb300 as spd
+    from paper_2207_13901_gb300.autotune import Autotuner
+    import tempfile
+    B = spd_synth.rmat_csr(20, 32, seed=0)
+    n, nnz = B.nrows, B.nnz
+    rng = np.random.default_rng(0)
+    sel = np.unique(rng.integers(0, nnz, 3000))
+    tuner = Autotuner(path=os.path.join(tempfile.mkdtemp(prefix="spd_tune_"), "a.json"), reps=2)
+    out = {"nrows": n, "nnz": nnz}
+    for K in (32, 128, 256):
+        C = spd_synth.normal((n, K), seed=10 + K, dtype=np.float32)
+        D = spd_synth.normal((n, K), seed=20 + K, dtype=np.float32)
+        for name, dt in (("f32", torch.float32), ("bf16", torch.bfloat16)):
+            dB = spd.CSR.from_host(B.pos, B.crd, B.vals, (n, n), dtype=dt)
+            Cd, Dd = torch.from_numpy(C).cuda().to(dt), torch.from_numpy(D).cuda().to(dt)
+            res = torch.empty(nnz, dtype=torch.float32, device="cuda")
+            best = tuner.sddmm(dB, Cd, Dd, force=True)
+            wsb = torch.empty(max(spd.csr_workspace_size(3, dB, best["split"], K, best["tune"], vtype=dt), 1),
+                              dtype=torch.uint8, device="cuda")
+            ms = _time_ms(lambda: spd.sddmm(dB, Cd, Dd, res, split=best["split"], tune=best["tune"], ws=wsb))
+            s = 2 if dt == torch.bfloat16 else 4
+            nb = 4 * (n + 1) + (4 + s + 4) * nnz + s * 2 * n * K
+            e = _entry(ms, nnz, nb, hbm)
+            e["tune"] = best
+            vr, Cr, Dr = _rounded(B.vals, dt), _rounded(C, dt), _rounded(D, dt)
+            ref = oracle.sddmm(B.pos, B.crd, vr, Cr, Dr, sel=sel, accurate=True)
+            sc = oracle.sddmm(B.pos, B.crd, np.abs(vr), np.abs(Cr), np.abs(Dr), sel=sel)
+            e["error"] = error_stats(res.double().cpu().numpy()[sel], ref, sc)
+            out["K%d_%s" % (K, name)] = e
+            del dB, Cd, Dd, res
+        if K == 128:
+            t = time.perf_counter()
+            oracle.sddmm(B.pos, B.crd, B.vals, C.astype(np.float64), D.astype(np.float64), sel=sel)
+            dt_o = time.perf_counter() - t
+            out["oracle_K128"] = {"nnz_per_s": sel.size / dt_o, "cores": 1, "sample": "%d sampled positions" % sel.size}
+    torch.cuda.empty_cache()
+    return out
+
+
+def row_backward(A, X32, hbm):
+    """SpMM backward on the 2^22 R-MAT with L = 128 in binary32: dvals = SDDMM(pattern,
+    dY, X) and dX = SpMM^T(A, dY) (torch.autograd through the hand-written backward)."""
+    import torch
+    import oracle
+    import paper_2207_13901_gb300 as spd
+    n, nnz, L = A.nrows, A.nnz, X32.shape[1]
+    dA = spd.CSR.from_host(A.pos, A.crd, A.vals, (n, n), dtype=torch.float32)
+    vals = dA.vals.clone().requires_grad_(True)
+    Xd = torch.from_numpy(X32).cuda().requires_grad_(True)
+    import spd_synth
+    W = torch.from_numpy(spd_synth.uniform((n, L), seed=7, dtype=np.float32)).cuda()
+    pattern = dA.with_vals(None)
+
+    def fwd_bwd():
+        vals.grad = None
+        Xd.grad = None
+        Y = spd.autograd.spmm(pattern.with_vals(vals), Xd)
+        Y.backward(W)
+
+    ms_all = _time_ms(fwd_bwd, reps=3, warm=1)
+    ms_sddmm = _time_ms(lambda: spd.sddmm(pattern, W, Xd.detach()), reps=3, warm=1)
+    ms_spmmt = _time_ms(lambda: spd.spmm_t(dA, W), reps=3, warm=1)
+    b_sddmm = 4 * (n + 1) + 8 * nnz + 4 * 2 * n * L
+    b_spmmt = 4 * (n + 1) + 8 * nnz + 4 * n * L + 4 * n * L
+    out = {"forward_backward_ms": round(ms_all, 3),
+           "sddmm_dvals": _entry(ms_sddmm, nnz, b_sddmm, hbm),
+           "spmm_t_dX": _entry(ms_spmmt, nnz, b_spmmt, hbm)}
+    rng = np.random.default_rng(1)
+    sel = np.unique(rng.integers(0, nnz, 2000))
+    Wh = W.cpu().numpy().astype(np.float64)
+    gv = vals.grad.double().cpu().numpy()
+    ref = oracle.sddmm(A.pos, A.crd, None, Wh, X32.astype(np.float64), sel=sel, accurate=True)
+    sc = oracle.sddmm(A.pos, A.crd, None, np.abs(Wh), np.abs(X32.astype(np.float64)), sel=sel)
+    out["sddmm_dvals"]["error"] = error_stats(gv[sel], ref, sc)
+    del dA, vals, Xd, W
+    torch.cuda.empty_cache()
+    return out
+
+
+def row_csf(hbm):
+    """SpTTV and SpMTTKRP (R = 32, 64) on the 2^17-cubed Zipf(1.1) CSF tensor with 50M
+    nonzeros, binary32 and bfloat16."""
+    import torch
+    import oracle
+    import spd_synth
+    import paper_2207_13901_gb300 as spd
+    t0 = time.time()
+    T = spd_synth.zipf_csf3((1 << 17,) * 3, 50_000_000, 1.1, seed=0)
+    out = {"nnz": T.nnz, "nfib": T.nfib, "generate_s": round(time.time() - t0, 1)}
+    I, J, K = T.dims
+    rng = np.random.default_rng(0)
+    fsel = np.unique(np.concatenate([rng.integers(0, T.nfib, 3000), np.argsort(np.diff(T.pos2))[-3:]]))
+    ssel = np.unique(rng.integers(2, I, 40))  # slices 0 and 1 hold millions of entries
+    c = spd_synth.normal(K, seed=31, dtype=np.float32)
+    for name, dt in (("f32", torch.float32), ("bf16", torch.bfloat16)):
+        dT = spd.CSF3.from_host(T.pos1, T.crd1, T.pos2, T.crd2, T.vals, T.dims, dtype=dt)
+        s = 2 if dt == torch.bfloat16 else 4
+        vr = _rounded(T.vals, dt)
+        cd = torch.from_numpy(c).cuda().to(dt)
+        o = torch.empty(T.nfib, dtype=torch.float32, device="cuda")
+        for split in ("nnz", "row"):
+            ws = torch.empty(max(spd.csf3_workspace_size(4, dT, split), 1), dtype=torch.uint8, device="cuda")
+            ms = _time_ms(lambda: spd.spttv(dT, cd, o, split=split, ws=ws))
+            nb = 4 * (T.nfib + 1) + (4 + s) * T.nnz + s * K + 4 * T.nfib
+            e = _entry(ms, T.nnz, nb, hbm)
+            cr = _rounded(c, dt)
+            ref = oracle.spttv(T.pos1, T.crd1, T.pos2, T.crd2, vr, cr, sel=fsel, accurate=True)
+            sc = oracle.spttv(T.pos1, T.crd1, T.pos2, T.crd2, np.abs(vr), np.abs(cr), sel=fsel)
+            e["error"] = error_stats(o.double().cpu().numpy()[fsel], ref, sc)
+            out["spttv_%s_%s" % (name, split)] = e
+        for R in (32, 64):
+            C = spd_synth.normal((J, R), seed=40 + R, dtype=np.float32)
+            D = spd_synth.normal((K, R), seed=50 + R, dtype=np.float32)
+            Cd, Dd = torch.from_numpy(C).cuda().to(dt), torch.from_numpy(D).cuda().to(dt)
+            Ao = torch.empty((I, R), dtype=torch.float32, device="cuda")
+            for split in ("nnz", "row"):
+                ws = torch.empty(max(spd.csf3_workspace_size(5, dT, split, R), 1), dtype=torch.uint8, device="cuda")
+                ms = _time_ms(lambda: spd.spmttkrp(dT, Cd, Dd, Ao, split=split, ws=ws))
+                nb = 4 * (I + 1) + 4 * T.nfib + 4 * (T.nfib + 1) + (4 + s) * T.nnz + s * (J + K) * R + 4 * I * R
+                e = _entry(ms, T.nnz, nb, hbm)
+                Cr, Dr = _rounded(C, dt), _rounded(D, dt)
+                ref = oracle.spmttkrp(T.pos1, T.crd1, T.pos2, T.crd2, vr, Cr, Dr, sel=ssel, accurate=True)
+                sc = oracle.spmttkrp(T.pos1, T.crd1, T.pos2, T.crd2, np.abs(vr), np.abs(Cr), np.abs(Dr), sel=ssel)
+                e["error"] = error_stats(Ao.double().cpu().numpy()[ssel], ref, sc)
+                out["spmttkrp_R%d_%s_%s" % (R, name, split)] = e
+            del Cd, Dd, Ao
+        del dT, o
+    t = time.perf_counter()
+    oracle.spttv(T.pos1, T.crd1, T.pos2, T.crd2, T.vals, c.astype(np.float64), sel=fsel)
+    dt_o = time.perf_counter() - t
+    snnz = int(np.diff(T.pos2)[fsel].sum())
+    out["oracle_spttv"] = {"nnz_per_s": snnz / dt_o, "cores": 1, "sample": "%d fibers" % fsel.size}
+    torch.cuda.empty_cache()
+    return out
+
+
+def row_batched(hbm):
+    """512 square CSR matrices (rows log-uniform in [1e3, 1e5], 4..64 uniform columns per
+    row), L = 64, binary32 and bfloat16: one persistent launch replayed from a CUDA graph
+    (policy and piece size autotuned) against 512 plain per-matrix launches."""
+    import torch
+    import oracle
+    import spd_synth
+    import paper_2207_13901_gb300 as spd
+    t0 = time.time()
+    mats = spd_synth.batched_uniform_csr(512, 1e3, 1e5, 4, 64, seed=0)
+    L = 64
+    rows = sum(A.nrows for A in mats)
+    nnz = sum(A.nnz for A in mats)
+    out = {"matrices": len(mats), "rows": rows, "nnz": nnz, "generate_s": round(time.time() - t0, 1)}
+    rng = np.random.default_rng(0)
+    Xh = [spd_synth.uniform((A.ncols, L), seed=1000 + m, dtype=np.float32) for m, A in enumerate(mats)]
+    check = sorted(set(rng.integers(0, len(mats), 6).tolist()))
+    for name, dt in (("f32", torch.float32), ("bf16", torch.bfloat16)):
+        dmats = [spd.CSR.from_host(A.pos, A.crd, A.vals, (A.nrows, A.ncols), dtype=dt) for A in mats]
+        Xs = [torch.from_numpy(X).cuda().to(dt) for X in Xh]
+        batch = spd.SpMMBatch(dmats, Xs)
+        best = batch.autotune(policies=("row", "auto"), units=(512, 1024, 2048), reps=3)
+        batch.capture()
+        s = 2 if dt == torch.bfloat16 else 4
+        nb = sum(4 * (A.nrows + 1) + (4 + s) * A.nnz + (s + 4) * A.nrows * L for A in mats)
+        ms_graph = _time_ms(batch.replay, reps=10)
+        ms_sep = _time_ms(lambda: batch.run_separately("row"), reps=3)
+        e = _entry(ms_graph, nnz, nb, hbm)
+        e["tune"] = best
+        e["separate_launches_ms"] = round(ms_sep, 3)
+        e["speedup_vs_separate"] = round(ms_sep / ms_graph, 3)
+        batch.replay()
+        torch.cuda.synchronize()
+        worst = 0.0
+        for m in check:
+            A = mats[m]
+            sel = np.unique(rng.integers(0, A.nrows, 200))
+            vr, Xr = _rounded(A.vals, dt), _rounded(Xh[m], dt)
+            ref = oracle.spmm(A.pos, A.crd, vr, Xr, sel=sel, accurate=True)
+            sc = oracle.spmm(A.pos, A.crd, np.abs(vr), np.abs(Xr), sel=sel)
+            worst = max(worst, error_stats(batch.Ys[m].double().cpu().numpy()[sel], ref, sc)["max"])
+        e["error"] = {"max": worst, "matrices_checked": check}
+        out[name] = e
+        del dmats, Xs, batch
+        torch.cuda.empty_cache()
+    return out
 
 
 # ----------------------------------------------------------------------------- CPU oracle

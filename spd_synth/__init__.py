@@ -195,35 +195,40 @@ def rmat_csr(scale: int, edge_factor: int = 16, a: float = 0.57, b: float = 0.19
     return CSR(n, n, pos.astype(np.int32), cols.astype(np.int32), vals)
 
 
-def _distinct_sorted_rows(rng: np.random.Generator, ncols: int, ks: np.ndarray) -> List[np.ndarray]:
-    """For every row q draw ks[q] distinct columns uniformly (first distinct draws), sorted."""
+def _distinct_sorted_rows(rng: np.random.Generator, ncols: int, ks: np.ndarray):
+    """For every row q draw ks[q] distinct columns uniformly at random, sorted.
+
+    Sparse rows (ks[q]^2 <= 4 ncols): whole-row rejection -- a row draws its ks[q] columns
+    i.i.d. and rows whose draws repeat a column are drawn again. Dense rows: the first
+    ks[q] columns of a random permutation (the order of ncols random keys). Either way
+    every row is a uniform random ks[q]-subset. Returns (columns, row offsets)."""
     nrows = ks.shape[0]
-    out_cols = np.empty(int(ks.sum()), dtype=np.int64)
     starts = np.zeros(nrows + 1, dtype=np.int64)
     np.cumsum(ks, out=starts[1:])
-    todo = np.arange(nrows)
+    kmax = int(ks.max()) if nrows else 0
+    out = np.empty((nrows, max(kmax, 1)), dtype=np.int64)
+    big = np.iinfo(np.int64).max
+    slot = np.arange(max(kmax, 1))[None, :]
+    dense = np.flatnonzero(ks * ks > 4 * ncols)
+    chunk = max(1, (1 << 24) // max(ncols, 1))
+    for c0 in range(0, dense.size, chunk):
+        rows_c = dense[c0:c0 + chunk]
+        perm = np.argsort(rng.random((rows_c.size, ncols)), axis=1, kind="stable")[:, :max(kmax, 1)]
+        perm[slot[:, :perm.shape[1]] >= ks[rows_c][:, None]] = big
+        perm.sort(axis=1)
+        out[rows_c, :perm.shape[1]] = perm
+    todo = np.flatnonzero(ks * ks <= 4 * ncols)
     while todo.size:
-        kmax = int(ks[todo].max()) if todo.size else 0
-        w = max(2 * kmax, kmax + 8)
-        cand = rng.integers(0, ncols, size=(todo.size, w), dtype=np.int64)
-        # first-occurrence mask in draw order
-        order = np.argsort(cand, axis=1, kind="stable")
-        sc = np.take_along_axis(cand, order, axis=1)
-        dup_sorted = np.zeros_like(sc, dtype=bool)
-        dup_sorted[:, 1:] = sc[:, 1:] == sc[:, :-1]
-        dup = np.zeros_like(dup_sorted)
-        np.put_along_axis(dup, order, dup_sorted, axis=1)
-        first = ~dup
-        rank = np.cumsum(first, axis=1)  # number of distinct values seen so far
-        need = ks[todo][:, None]
-        take = first & (rank <= need)
-        ok = take.sum(axis=1) == ks[todo]
-        for q_local in np.flatnonzero(ok):
-            q = todo[q_local]
-            vals = np.sort(cand[q_local][take[q_local]])
-            out_cols[starts[q]:starts[q + 1]] = vals
-        todo = todo[~ok]
-    return out_cols, starts
+        cand = rng.integers(0, ncols, size=(todo.size, max(kmax, 1)), dtype=np.int64)
+        cand[slot >= ks[todo][:, None]] = big
+        cand.sort(axis=1)
+        dup = (cand[:, 1:] == cand[:, :-1]) & (cand[:, 1:] != big)
+        bad = dup.any(axis=1)
+        good = ~bad
+        out[todo[good]] = cand[good]
+        todo = todo[bad]
+    cols = out[slot < ks[:, None]] if nrows else np.zeros(0, dtype=np.int64)
+    return cols, starts
 
 
 def uniform_csr(nrows: int, ncols: int, nnz_per_row, seed: int = 0,

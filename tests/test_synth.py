@@ -1,0 +1,48 @@
+"""The input generators: level-format invariants, determinism, and termination on the
+small and dense shapes the tests use (no GPU)."""
+import numpy as np
+import pytest
+
+import oracle
+import spd_synth
+
+
+def _valid(A):
+    assert A.pos[0] == 0 and A.pos[-1] == A.nnz and np.all(np.diff(A.pos) >= 0)
+    assert oracle.validate_level(A.nrows, A.ncols, A.pos, A.crd) == (0, -1)
+    for i in range(min(A.nrows, 300)):
+        seg = A.crd[A.pos[i]:A.pos[i + 1]]
+        assert np.all(np.diff(seg) > 0)  # sorted, distinct
+
+
+@pytest.mark.parametrize("shape", [(100, 100, (4, 64)), (50, 64, 64), (4096, 4096, 16), (10, 1, 1), (7, 3, (0, 3))])
+def test_uniform_csr_shapes(shape):
+    n, m, k = shape
+    A = spd_synth.uniform_csr(n, m, k, seed=1)
+    _valid(A)
+    lens = np.diff(A.pos)
+    if isinstance(k, tuple):
+        assert lens.min() >= min(k[0], m) and lens.max() <= min(k[1], m)
+    else:
+        assert np.all(lens == min(k, m))
+    B = spd_synth.uniform_csr(n, m, k, seed=1)
+    assert np.array_equal(A.crd, B.crd) and np.array_equal(A.vals, B.vals)
+
+
+def test_batched_small_and_dense():
+    mats = spd_synth.batched_uniform_csr(24, 1e2, 3e3, 4, 64, seed=1)
+    assert len(mats) == 24
+    for A in mats:
+        assert A.nrows == A.ncols and 100 <= A.nrows <= 3000
+        _valid(A)
+
+
+def test_rmat_and_zipf_invariants():
+    A = spd_synth.rmat_csr(12, 16, seed=1)
+    _valid(A)
+    assert A.nnz > 0.9 * 16 * 4096 * 0.9
+    T = spd_synth.zipf_csf3((1 << 8,) * 3, 20000, seed=2)
+    assert T.nnz == 20000
+    assert oracle.validate_level(T.dims[0], T.dims[1], T.pos1, T.crd1) == (0, -1)
+    assert oracle.validate_level(T.nfib, T.dims[2], T.pos2, T.crd2) == (0, -1)
+    assert np.all(np.diff(T.pos2) > 0)  # no empty fibers
