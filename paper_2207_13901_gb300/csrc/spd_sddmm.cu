@@ -3,13 +3,18 @@
 // The output keeps B's coordinate structure (Section V-B): one value per stored
 // position p of B, so the work is a stream over B's positions with two gathered dense
 // rows per position: row i of C and row j of D, with D passed transposed as
-// Dnk[j,k] = D(k,j) so that both rows are contiguous. One warp consumes one piece of
-// the flattened coordinate tree (rows and positions balanced together); its lanes span
-// K in vectors of EPL elements, U positions are in flight at once, and each dot product
-// is finished with a butterfly reduction across the warp.
+// Dnk[j,k] = D(k,j) so that both rows are contiguous.
 //
-// The contraction over k is a dot product per stored position (a matrix-vector shape
-// with no reuse of D rows inside a warp), so it stays on the CUDA cores: at about
+// One warp consumes one piece of the flattened coordinate tree (rows and positions
+// balanced together). Positions come in windows of 32: each lane loads one position's
+// crd/vals and finds its row with a search over a 32-row window of pos held across the
+// lanes; the window for the next rows is fetched while the current window is consumed.
+// Lanes form groups of G (G * EPL covers K, EPL elements per 16-byte vector), so a warp
+// step covers 32/G positions; U steps are in flight, and the U partial dot products of
+// a lane are reduced across the group together by a halving butterfly.
+//
+// The contraction over k is one dot product per stored position (a matrix-vector
+// shape, no reuse of D rows inside a warp), so it stays on the CUDA cores: at about
 // 0.5 flop per gathered byte it is bound by the gathers, not by arithmetic.
 #include "spd_internal.cuh"
 
@@ -17,7 +22,84 @@ namespace spd {
 
 constexpr unsigned FULLM = 0xffffffffu;
 
-template <typename VT, int EPL, int U>
+// Rows of the positions pb + lane: lane q of the window holds the end of row rw + q.
+struct PosRows {
+    int32_t rw;
+    int32_t wend;
+    __device__ __forceinline__ void load(int32_t base, int64_t n, const int32_t *pos, int lane) {
+        rw = base;
+        wend = ((int64_t)base + lane < n) ? ld_stream(pos + base + lane + 1) : INT_MAX;
+    }
+    // Row of position P for every lane with `valid` (the rows must be >= rw).
+    __device__ __forceinline__ int32_t find(int32_t P, bool valid, int64_t n, const int32_t *pos, int lane) {
+        int32_t row = 0;
+        bool done = !valid;
+        while (true) {
+            // number of window rows that end at or before P (0..32); every lane takes part
+            // in every shuffle (the full mask requires it), the lane's own test follows
+            int lo = __shfl_sync(FULLM, wend, 31) <= P ? 32 : 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const int32_t w = __shfl_sync(FULLM, wend, (lo + step - 1) & 31);
+                if (lo < 32 && w <= P) lo += step;
+            }
+            if (!done && lo < 32) {
+                row = rw + lo;
+                done = true;
+            }
+            if (!__any_sync(FULLM, !done)) break;
+            load(rw + 32, n, pos, lane);
+        }
+        return row;
+    }
+};
+
+// Sums each of the U values of every lane over its group of G lanes. Returns, in each
+// lane, the total of value u_of(lane) (see below); all values are summed exactly once.
+template <int G, int U, typename T>
+__device__ __forceinline__ T group_reduce(T (&v)[U], int lane) {
+    int count = U;
+#pragma unroll
+    for (int off = G / 2; off >= 1; off >>= 1) {
+        if (count > 1) {
+            const int half = count / 2;
+            const bool upper = (lane & off) != 0;
+#pragma unroll
+            for (int i = 0; i < U / 2; ++i) {
+                if (i < half) {
+                    const T send = upper ? v[i] : v[half + i];
+                    const T keep = upper ? v[half + i] : v[i];
+                    v[i] = keep + __shfl_xor_sync(FULLM, send, off);
+                }
+            }
+            count = half;
+        } else {
+            v[0] += __shfl_xor_sync(FULLM, v[0], off);
+        }
+    }
+    return v[0];
+}
+
+// Which of the U values a lane holds after group_reduce, and whether it writes it.
+template <int G, int U>
+__device__ __forceinline__ int reduced_index(int lane, bool &writer) {
+    int u = 0, count = U, last = G;
+#pragma unroll
+    for (int off = G / 2; off >= 1; off >>= 1) {
+        if (count > 1) {
+            const int half = count / 2;
+            if (lane & off) u += half;
+            count = half;
+            last = off;
+        }
+    }
+    // after the halving steps the remaining butterfly makes every lane of a block of
+    // `last` lanes hold the same total; the first lane of each block writes it
+    writer = U == 1 ? (lane % G) == 0 : (lane & (last - 1)) == 0;
+    return u;
+}
+
+template <typename VT, int EPL, int G>
 __global__ void __launch_bounds__(256) sddmm_warp_kernel(
     int64_t n, const int32_t *__restrict__ pos, const int32_t *__restrict__ crd, const VT *__restrict__ vals,
     const VT *__restrict__ C, int64_t ldc, const VT *__restrict__ Dnk, int64_t ldd, int64_t K,
@@ -25,88 +107,81 @@ __global__ void __launch_bounds__(256) sddmm_warp_kernel(
     int64_t npieces, int64_t P) {
     using AT = typename Traits<VT>::acc;
     using OT = typename Traits<VT>::out;
+    constexpr int NPG = 32 / G;                             // positions per warp step
+    constexpr int U = G == 32 ? 4 : 2;                      // warp steps in flight
+    __shared__ int32_t s_crd_all[8][32], s_row_all[8][32];  // one window per warp (<= 8 warps)
+    __shared__ AT s_val_all[8][32];
     const int lane = threadIdx.x & 31;
-    const int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int wid = threadIdx.x >> 5;
+    const int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid;
     if (c >= (prow ? npieces : P)) return;
     const PieceBounds b = prow ? nnz_piece(c, prow, ppos) : row_piece(c, P, n, pos);
-    const int64_t ktiles = (K + 32 * EPL - 1) / (32 * EPL);
+    int32_t *s_crd = s_crd_all[wid];
+    int32_t *s_row = s_row_all[wid];
+    AT *s_val = s_val_all[wid];
+    const int gi = lane / G;  // group of this lane
+    const int gl = lane % G;  // lane inside the group
+    bool writer;
+    const int my_u = reduced_index<G, U>(gl, writer);
+    const int64_t ktiles = (K + G * EPL - 1) / (G * EPL);
 
-    int32_t r = b.r0;
-    int32_t rw = r;
-    int32_t wend = ((int64_t)rw + lane < n) ? ld_stream(pos + rw + lane + 1) : INT_MAX;
-    int32_t cur_end = r < n ? __shfl_sync(FULLM, wend, 0) : INT_MAX;
-
+    PosRows pr;
+    pr.load(b.r0, n, pos, lane);
     for (int32_t pb = b.p0; pb < b.p1; pb += 32) {
         const int cnt = (b.p1 - pb) < 32 ? (b.p1 - pb) : 32;
-        int32_t c_l = 0;
-        AT v_l = 1;
-        if (lane < cnt) {
-            c_l = ld_stream(crd + pb + lane);
-            if (vals) v_l = (AT)ld_stream(vals + pb + lane);
-        }
-        for (int j0 = 0; j0 < cnt; j0 += U) {
-            int32_t rowu[U], colu[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int j = j0 + u;
-                colu[u] = __shfl_sync(FULLM, c_l, j & 31);
-                if (j < cnt) {
-                    const int32_t pj = pb + j;
-                    while (cur_end <= pj) {
-                        ++r;
-                        if (r - rw == 32) {
-                            rw = r;
-                            wend = ((int64_t)rw + lane < n) ? ld_stream(pos + rw + lane + 1) : INT_MAX;
-                        }
-                        cur_end = r < n ? __shfl_sync(FULLM, wend, r - rw) : INT_MAX;
-                    }
-                }
-                rowu[u] = r;
-            }
+        const bool valid = lane < cnt;
+        const int32_t my_crd = valid ? ld_stream(crd + pb + lane) : 0;
+        const AT my_val = (valid && vals) ? (AT)ld_stream(vals + pb + lane) : (AT)1;
+        const int32_t my_row = pr.find(pb + lane, valid, n, pos, lane);
+        __syncwarp();
+        s_crd[lane] = my_crd;
+        s_row[lane] = my_row;
+        s_val[lane] = my_val;
+        __syncwarp();
+        // next window starts at the last row of this one (fetched while this one is used)
+        const int32_t next_rw = __shfl_sync(FULLM, my_row, cnt - 1);
+        if (next_rw != pr.rw) pr.load(next_rw, n, pos, lane);
+#pragma unroll 1
+        for (int j0 = 0; j0 < cnt; j0 += NPG * U) {
             AT part[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) part[u] = 0;
+#pragma unroll 1
             for (int64_t kt = 0; kt < ktiles; ++kt) {
-                const int64_t k = kt * (32 * EPL) + (int64_t)lane * EPL;
+                const int64_t k = kt * (G * EPL) + (int64_t)gl * EPL;
                 if (k < K) {
-                    AT dv[U][EPL], cv[U][EPL];
+                    AT cv[U][EPL], dv[U][EPL];
 #pragma unroll
                     for (int u = 0; u < U; ++u) {
-                        if (j0 + u < cnt) {
-                            ld_vec<EPL>(Dnk + (int64_t)colu[u] * ldd + k, dv[u]);
-                            ld_vec<EPL>(C + (int64_t)rowu[u] * ldc + k, cv[u]);
+                        const int j = j0 + u * NPG + gi;
+                        if (j < cnt) {
+                            ld_vec<EPL>(C + (int64_t)s_row[j] * ldc + k, cv[u]);
+                            ld_vec<EPL>(Dnk + (int64_t)s_crd[j] * ldd + k, dv[u]);
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < EPL; ++e) cv[u][e] = dv[u][e] = 0;
                         }
                     }
 #pragma unroll
                     for (int u = 0; u < U; ++u) {
-                        if (j0 + u < cnt) {
 #pragma unroll
-                            for (int e = 0; e < EPL; ++e) part[u] = fma(cv[u][e], dv[u][e], part[u]);
-                        }
+                        for (int e = 0; e < EPL; ++e) part[u] = fma(cv[u][e], dv[u][e], part[u]);
                     }
                 }
             }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) part[u] += __shfl_xor_sync(FULLM, part[u], off);
-            }
-            AT mine = 0;
-#pragma unroll
-            for (int u = 0; u < U; ++u)
-                if (lane == u) mine = part[u];
-            const AT bv = __shfl_sync(FULLM, v_l, (j0 + lane) & 31);
-            if (lane < U && j0 + lane < cnt) __stcs(out + pb + j0 + lane, (OT)(bv * mine));
+            const AT tot = group_reduce<G, U>(part, gl);
+            const int j = j0 + my_u * NPG + gi;
+            if (writer && j < cnt) __stcs(out + pb + j, (OT)(s_val[j] * tot));
         }
     }
 }
 
-template <typename VT, int EPL>
-static spd_status launch_sddmm_epl(const spd_csr *B, const void *C, int64_t K, int64_t ldc, const void *Dnk,
-                                   int64_t ldd, void *outv, int split, const Tuning &tn, void *ws, cudaStream_t st) {
+template <typename VT, int EPL, int G>
+static spd_status launch_sddmm_g(const spd_csr *B, const void *C, int64_t K, int64_t ldc, const void *Dnk,
+                                 int64_t ldd, void *outv, int split, const Tuning &tn, void *ws, cudaStream_t st) {
     using OT = typename Traits<VT>::out;
-    constexpr int U = EPL >= 8 ? 4 : 8;
-    const int wpb = tn.block_threads / 32;
+    const int threads = tn.block_threads > 256 ? 256 : tn.block_threads;  // shared windows for <= 8 warps
+    const int wpb = threads / 32;
     const VT *v = static_cast<const VT *>(B->vals);
     const VT *cc = static_cast<const VT *>(C);
     const VT *dd = static_cast<const VT *>(Dnk);
@@ -114,7 +189,7 @@ static spd_status launch_sddmm_epl(const spd_csr *B, const void *C, int64_t K, i
     if (split == SPD_SPLIT_ROW) {
         int64_t P = tn.row_pieces > 0 ? tn.row_pieces : ceil_div(B->nrows + B->nnz, tn.unit_items);
         if (P < 1) P = 1;
-        sddmm_warp_kernel<VT, EPL, U><<<(unsigned)ceil_div(P, wpb), tn.block_threads, 0, st>>>(
+        sddmm_warp_kernel<VT, EPL, G><<<(unsigned)ceil_div(P, wpb), threads, 0, st>>>(
             B->nrows, B->pos, B->crd, v, cc, ldc, dd, ldd, K, o, nullptr, nullptr, 0, P);
         return check_launch("sddmm_warp_kernel(row)");
     }
@@ -124,25 +199,29 @@ static spd_status launch_sddmm_epl(const spd_csr *B, const void *C, int64_t K, i
     int32_t *ppos = reinterpret_cast<int32_t *>(w + Lw.part_pos);
     spd_status s = launch_merge_partition(B->nrows, B->nnz, B->pos, tn.unit_items, Lw.npieces, prow, ppos, st);
     if (s) return s;
-    sddmm_warp_kernel<VT, EPL, U><<<(unsigned)ceil_div(Lw.npieces, wpb), tn.block_threads, 0, st>>>(
+    sddmm_warp_kernel<VT, EPL, G><<<(unsigned)ceil_div(Lw.npieces, wpb), threads, 0, st>>>(
         B->nrows, B->pos, B->crd, v, cc, ldc, dd, ldd, K, o, prow, ppos, Lw.npieces, 0);
     return check_launch("sddmm_warp_kernel(nnz)");
+}
+
+// Group width: the power of two in [4, 32] closest to covering K with EPL-element vectors.
+template <typename VT, int EPL>
+static spd_status launch_sddmm_epl(const spd_csr *B, const void *C, int64_t K, int64_t ldc, const void *Dnk,
+                                   int64_t ldd, void *outv, int split, const Tuning &tn, void *ws, cudaStream_t st) {
+    const int64_t lanes = ceil_div(K > 0 ? K : 1, EPL);
+    if (lanes <= 4) return launch_sddmm_g<VT, EPL, 4>(B, C, K, ldc, Dnk, ldd, outv, split, tn, ws, st);
+    if (lanes <= 8) return launch_sddmm_g<VT, EPL, 8>(B, C, K, ldc, Dnk, ldd, outv, split, tn, ws, st);
+    if (lanes <= 16) return launch_sddmm_g<VT, EPL, 16>(B, C, K, ldc, Dnk, ldd, outv, split, tn, ws, st);
+    return launch_sddmm_g<VT, EPL, 32>(B, C, K, ldc, Dnk, ldd, outv, split, tn, ws, st);
 }
 
 template <typename VT>
 static spd_status launch_sddmm(const spd_csr *B, const void *C, int64_t K, int64_t ldc, const void *Dnk, int64_t ldd,
                                void *outv, int split, const Tuning &tn, void *ws, cudaStream_t st) {
-    int e1 = pick_epl(K, sizeof(VT), sizeof(VT), C, ldc, nullptr, ldc);
-    int e2 = pick_epl(K, sizeof(VT), sizeof(VT), Dnk, ldd, nullptr, ldd);
-    int epl = e1 < e2 ? e1 : e2;
-    switch (epl) {
-        case 1: return launch_sddmm_epl<VT, 1>(B, C, K, ldc, Dnk, ldd, outv, split, tn, ws, st);
-        case 2: return launch_sddmm_epl<VT, 2>(B, C, K, ldc, Dnk, ldd, outv, split, tn, ws, st);
-        case 4: return launch_sddmm_epl<VT, 4>(B, C, K, ldc, Dnk, ldd, outv, split, tn, ws, st);
-        default:
-            if constexpr (sizeof(VT) <= 4) return launch_sddmm_epl<VT, 8>(B, C, K, ldc, Dnk, ldd, outv, split, tn, ws, st);
-            return launch_sddmm_epl<VT, 4>(B, C, K, ldc, Dnk, ldd, outv, split, tn, ws, st);
-    }
+    constexpr int V = 16 / sizeof(VT);  // elements of one 16-byte vector
+    const bool vec = K % V == 0 && ldc % V == 0 && ldd % V == 0 && aligned(C, 16) && aligned(Dnk, 16);
+    if (vec) return launch_sddmm_epl<VT, V>(B, C, K, ldc, Dnk, ldd, outv, split, tn, ws, st);
+    return launch_sddmm_epl<VT, 1>(B, C, K, ldc, Dnk, ldd, outv, split, tn, ws, st);
 }
 
 }  // namespace spd
