@@ -182,6 +182,86 @@ __device__ __forceinline__ PieceBounds nnz_piece(int64_t c, const int32_t *prow,
     return b;
 }
 
+// Lane-parallel lookup of the parent of 32 children at once. Lane q of the window holds
+// the end (in children) of parent rw + q; find() returns, for each lane, the parent
+// whose child range holds the lane's child P, advancing the window as needed (parents
+// must be >= rw).
+struct PosRows {
+    int32_t rw;
+    int32_t wend;
+    __device__ __forceinline__ void load(int32_t base, int64_t n, const int32_t *pos, int lane) {
+        rw = base;
+        wend = ((int64_t)base + lane < n) ? ld_stream(pos + base + lane + 1) : INT_MAX;
+    }
+    // Row of position P for every lane with `valid` (the rows must be >= rw).
+    __device__ __forceinline__ int32_t find(int32_t P, bool valid, int64_t n, const int32_t *pos, int lane) {
+        int32_t row = 0;
+        bool done = !valid;
+        while (true) {
+            // number of window rows that end at or before P (0..32); every lane takes part
+            // in every shuffle (the full mask requires it), the lane's own test follows
+            int lo = __shfl_sync(0xffffffffu, wend, 31) <= P ? 32 : 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const int32_t w = __shfl_sync(0xffffffffu, wend, (lo + step - 1) & 31);
+                if (lo < 32 && w <= P) lo += step;
+            }
+            if (!done && lo < 32) {
+                row = rw + lo;
+                done = true;
+            }
+            if (!__any_sync(0xffffffffu, !done)) break;
+            load(rw + 32, n, pos, lane);
+        }
+        return row;
+    }
+};
+
+// Sums each of the U values of every lane over its group of G lanes. Returns, in each
+// lane, the total of value u_of(lane) (see below); all values are summed exactly once.
+template <int G, int U, typename T>
+__device__ __forceinline__ T group_reduce(T (&v)[U], int lane) {
+    int count = U;
+#pragma unroll
+    for (int off = G / 2; off >= 1; off >>= 1) {
+        if (count > 1) {
+            const int half = count / 2;
+            const bool upper = (lane & off) != 0;
+#pragma unroll
+            for (int i = 0; i < U / 2; ++i) {
+                if (i < half) {
+                    const T send = upper ? v[i] : v[half + i];
+                    const T keep = upper ? v[half + i] : v[i];
+                    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+                }
+            }
+            count = half;
+        } else {
+            v[0] += __shfl_xor_sync(0xffffffffu, v[0], off);
+        }
+    }
+    return v[0];
+}
+
+// Which of the U values a lane holds after group_reduce, and whether it writes it.
+template <int G, int U>
+__device__ __forceinline__ int reduced_index(int lane, bool &writer) {
+    int u = 0, count = U, last = G;
+#pragma unroll
+    for (int off = G / 2; off >= 1; off >>= 1) {
+        if (count > 1) {
+            const int half = count / 2;
+            if (lane & off) u += half;
+            count = half;
+            last = off;
+        }
+    }
+    // after the halving steps the remaining butterfly makes every lane of a block of
+    // `last` lanes hold the same total; the first lane of each block writes it
+    writer = U == 1 ? (lane % G) == 0 : (lane & (last - 1)) == 0;
+    return u;
+}
+
 // ------------------------------------------------------------------ host plumbing
 
 constexpr size_t kAlign = 256;

@@ -1,29 +1,24 @@
 // spd_mttkrp.cu -- SpMTTKRP A(i,l) = B(i,j,k) * C(j,l) * D(k,l) (Section VI-A) on a
 // CSF tensor B = {Dense, Compressed, Compressed}.
 //
-// Per fiber (i,j): t(l) = sum_k B(i,j,k) D(k,l); then A(i,l) += C(j,l) t(l). One warp
-// consumes one piece; lanes span R in vectors of EPL elements.
+// Every entry (i,j,k) contributes (B(i,j,k) * C(j,:)) * D(k,:) to row i of A, formed in
+// the order the statement is written. One warp consumes one piece of entries; entries
+// come in windows of 32 whose fiber (hence j) and slice (i) each lane finds with a
+// lane-parallel search over 32-entry windows of pos2 and pos1. Lanes form groups of G
+// (G * EPL covers R), so a warp step covers 32/G entries; the groups' partial rows are
+// summed across the warp only when the slice changes.
 //   Nnz split (the GPU schedule of Section VI-A): coordinate fusion of levels 2 and 3 and
 //     a non-zero partition of the fused items (each fiber's entries followed by one
-//     "fiber end" item), so pieces balance entries and fibers. The partial fiber at a
-//     piece end is folded into the piece's slice partial (by linearity in t), and the
-//     slice partial at a piece end goes to a binary64 carry added by the fix-up kernel.
-//     Piece c writes the slices [s_c, s_{c+1}) whose last fiber ends inside it, where
-//     s_c = #{i : pos1[i+1] <= first fiber of piece c} (s_0 = 0, s_last = I).
+//     "fiber end" item), so pieces balance entries and fibers. Piece c writes the slices
+//     [s_c, s_{c+1}) whose last fiber ends inside it, where s_c = #{i : pos1[i+1] <= first
+//     fiber of piece c} (s_0 = 0, s_last = I); the partial of the slice a piece ends in
+//     is a binary64 carry added by the fix-up kernel.
 //   Row split: universe partition of the slices, [floor(c I/P), floor((c+1) I/P)).
 // The contraction per entry is a scaled row of D (no dense reuse within a warp), so the
 // work stays on the CUDA cores.
 #include "spd_internal.cuh"
 
 namespace spd {
-
-constexpr unsigned FULLK = 0xffffffffu;
-
-template <typename T, int N>
-__device__ __forceinline__ void zero_k(T (&a)[N]) {
-#pragma unroll
-    for (int e = 0; e < N; ++e) a[e] = (T)0;
-}
 
 // s_c for every interior piece boundary: the number of slices whose end (pos1[i+1])
 // is at or before the piece's first fiber. Binary search over pos1[1..I].
@@ -49,7 +44,7 @@ __global__ void slice_partition_kernel(int64_t I, const int32_t *__restrict__ po
     pslice[c] = (int32_t)lo;
 }
 
-template <typename VT, int EPL, int U>
+template <typename VT, int EPL, int G>
 __global__ void __launch_bounds__(256) spmttkrp_warp_kernel(
     int64_t I, int64_t F, const int32_t *__restrict__ pos1, const int32_t *__restrict__ crd1,
     const int32_t *__restrict__ pos2, const int32_t *__restrict__ crd2, const VT *__restrict__ vals,
@@ -59,10 +54,16 @@ __global__ void __launch_bounds__(256) spmttkrp_warp_kernel(
     int32_t *__restrict__ carry_row, double *__restrict__ carry_val) {
     using AT = typename Traits<VT>::acc;
     using OT = typename Traits<VT>::out;
+    constexpr int NPG = 32 / G;         // entries per warp step
+    constexpr int U = G == 32 ? 4 : 2;  // warp steps in flight
+    __shared__ int32_t s_j_all[8][32], s_k_all[8][32], s_sl_all[8][32];
+    __shared__ AT s_v_all[8][32];
     const int lane = threadIdx.x & 31;
-    const int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int wid = threadIdx.x >> 5;
+    const int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid;
     if (c >= (pfib ? npieces : P)) return;
-    const int64_t col = (int64_t)blockIdx.y * (32 * EPL) + (int64_t)lane * EPL;
+    const int gi = lane / G, gl = lane % G;
+    const int64_t col = (int64_t)blockIdx.y * (G * EPL) + (int64_t)gl * EPL;
     const bool active = col < R;
 
     int32_t f0, p0, f1, p1, s0, s1;
@@ -81,131 +82,121 @@ __global__ void __launch_bounds__(256) spmttkrp_warp_kernel(
         p0 = __ldg(pos2 + f0);
         p1 = __ldg(pos2 + f1);
     }
+    (void)f1;
+    int32_t *s_j = s_j_all[wid], *s_k = s_k_all[wid], *s_sl = s_sl_all[wid];
+    AT *s_v = s_v_all[wid];
 
-    AT t[EPL], a[EPL];
-    zero_k(t);
-    zero_k(a);
-    bool dirty = false;  // a holds contributions not yet written
-
-    // slice-end window: lane q holds pos1[sw + q + 1]
-    int32_t i = s0, sw = s0;
-    int32_t send = ((int64_t)sw + lane < I) ? __ldg(pos1 + sw + lane + 1) : INT_MAX;
-    // fiber windows: lane q holds the end of fiber fw + q and its j coordinate
-    int32_t f = f0, fw = f0;
-    int32_t fend = ((int64_t)fw + lane < F) ? ld_stream(pos2 + fw + lane + 1) : INT_MAX;
-    int32_t fj = ((int64_t)fw + lane < F) ? ld_stream(crd1 + fw + lane) : 0;
-    int32_t cur_fend = f < f1 ? __shfl_sync(FULLK, fend, 0) : INT_MAX;
-
-    auto emit_ready = [&]() {  // write every owned slice whose last fiber is done
-        while (i < s1) {
-            const int32_t e = __shfl_sync(FULLK, send, i - sw);
-            if (e > f) break;
-            if (active) {
-                OT o[EPL];
+    AT acc[EPL];
 #pragma unroll
-                for (int q = 0; q < EPL; ++q) o[q] = (OT)a[q];
-                st_vec(A + (int64_t)i * lda + col, o);
-            }
-            zero_k(a);
-            dirty = false;
-            ++i;
-            if (i - sw == 32) {
-                sw = i;
-                send = ((int64_t)sw + lane < I) ? __ldg(pos1 + sw + lane + 1) : INT_MAX;
-            }
-        }
-    };
-    auto finish_fiber = [&]() {  // a += C(j,:) * t for the current fiber f
-        const int32_t j = __shfl_sync(FULLK, fj, f - fw);
-        if (active) {
-            AT cv[EPL];
-            ld_vec<EPL>(C + (int64_t)j * ldc + col, cv);
+    for (int e = 0; e < EPL; ++e) acc[e] = 0;
+    bool dirty = false;  // acc holds contributions
+    int32_t cs = s0;     // slice being accumulated (the same in every lane)
+
+    // total of acc over the groups of the warp (every lane ends with it)
+    auto warp_total = [&](AT (&t)[EPL]) {
 #pragma unroll
-            for (int q = 0; q < EPL; ++q) a[q] = fma(cv[q], t[q], a[q]);
+        for (int e = 0; e < EPL; ++e) {
+            t[e] = acc[e];
+#pragma unroll
+            for (int off = G; off < 32; off <<= 1) t[e] += __shfl_xor_sync(0xffffffffu, t[e], off);
         }
-        zero_k(t);
-        dirty = true;
     };
-    auto next_fiber = [&]() {
-        ++f;
-        if (f - fw == 32) {
-            fw = f;
-            fend = ((int64_t)fw + lane < F) ? ld_stream(pos2 + fw + lane + 1) : INT_MAX;
-            fj = ((int64_t)fw + lane < F) ? ld_stream(crd1 + fw + lane) : 0;
+    // slice cs is complete: write it, then zeros for the empty slices before `next`
+    auto finish_to = [&](int32_t next) {
+        AT t[EPL];
+        warp_total(t);
+        if (gi == 0 && active) {
+            OT o[EPL];
+#pragma unroll
+            for (int e = 0; e < EPL; ++e) o[e] = (OT)t[e];
+            st_vec(A + (int64_t)cs * lda + col, o);
+#pragma unroll
+            for (int e = 0; e < EPL; ++e) o[e] = (OT)0;
+            const int32_t stop = next < s1 ? next : s1;
+            for (int32_t i = cs + 1; i < stop; ++i) st_vec(A + (int64_t)i * lda + col, o);
         }
-        cur_fend = f < f1 ? __shfl_sync(FULLK, fend, f - fw) : INT_MAX;
+#pragma unroll
+        for (int e = 0; e < EPL; ++e) acc[e] = 0;
+        dirty = false;
+        cs = next;
     };
 
-    emit_ready();
+    PosRows fw, sw;  // fiber ends (in entries) and slice ends (in fibers)
+    fw.load(f0, F, pos2, lane);
+    sw.load(s0, I, pos1, lane);
     for (int32_t pb = p0; pb < p1; pb += 32) {
         const int cnt = (p1 - pb) < 32 ? (p1 - pb) : 32;
-        int32_t k_l = 0;
-        AT v_l = 0;
-        if (lane < cnt) {
-            k_l = ld_stream(crd2 + pb + lane);
-            v_l = (AT)ld_stream(vals + pb + lane);
-        }
-        for (int j0 = 0; j0 < cnt; j0 += U) {
-            AT dv[U][EPL];
+        const bool valid = lane < cnt;
+        const int32_t my_k = valid ? ld_stream(crd2 + pb + lane) : 0;
+        const AT my_v = valid ? (AT)ld_stream(vals + pb + lane) : (AT)0;
+        const int32_t my_f = fw.find(pb + lane, valid, F, pos2, lane);
+        const int32_t my_sl = sw.find(my_f, valid, I, pos1, lane);
+        const int32_t my_j = valid ? __ldg(crd1 + my_f) : 0;
+        __syncwarp();
+        s_j[lane] = my_j;
+        s_k[lane] = my_k;
+        s_sl[lane] = my_sl;
+        s_v[lane] = my_v;
+        __syncwarp();
+        const int32_t nf = __shfl_sync(0xffffffffu, my_f, cnt - 1);
+        const int32_t ns = __shfl_sync(0xffffffffu, my_sl, cnt - 1);
+        if (nf != fw.rw) fw.load(nf, F, pos2, lane);
+        if (ns != sw.rw) sw.load(ns, I, pos1, lane);
+        int a = 0;
+        while (a < cnt) {  // segments of entries that share a slice
+            const int32_t seg = s_sl[a];
+            const unsigned other = __ballot_sync(0xffffffffu, valid && lane >= a && my_sl != seg);
+            const int bnd = other ? __ffs(other) - 1 : cnt;
+            if (seg != cs) finish_to(seg);
+#pragma unroll 1
+            for (int t0 = a; t0 < bnd; t0 += NPG * U) {
+                AT cv[U][EPL], dv[U][EPL];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int32_t kk = __shfl_sync(FULLK, k_l, (j0 + u) & 31);
-                if (active && j0 + u < cnt) ld_vec<EPL>(D + (int64_t)kk * ldd + col, dv[u]);
-                else zero_k(dv[u]);
-            }
+                for (int u = 0; u < U; ++u) {
+                    const int j = t0 + u * NPG + gi;
+                    if (active && j < bnd) {
+                        ld_vec<EPL>(C + (int64_t)s_j[j] * ldc + col, cv[u]);
+                        ld_vec<EPL>(D + (int64_t)s_k[j] * ldd + col, dv[u]);
+                    } else {
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int j = j0 + u;
-                const AT vj = __shfl_sync(FULLK, v_l, j & 31);
-                if (j < cnt) {
-                    const int32_t pj = pb + j;
-                    while (cur_fend <= pj) {
-                        finish_fiber();
-                        next_fiber();
-                        emit_ready();
+                        for (int e = 0; e < EPL; ++e) cv[u][e] = dv[u][e] = 0;
                     }
+                }
 #pragma unroll
-                    for (int q = 0; q < EPL; ++q) t[q] = fma(vj, dv[u][q], t[q]);
-                    dirty = true;
+                for (int u = 0; u < U; ++u) {
+                    const int j = t0 + u * NPG + gi;
+                    const AT v = j < bnd ? s_v[j] : (AT)0;
+#pragma unroll
+                    for (int e = 0; e < EPL; ++e) acc[e] = fma(v * cv[u][e], dv[u][e], acc[e]);
                 }
             }
-        }
-    }
-    while (f < f1) {  // fibers ending at or after the last entry of the piece
-        finish_fiber();
-        next_fiber();
-        emit_ready();
-    }
-    if (pfib) {
-        // the piece may end inside fiber f1: fold its partial into the slice partial
-        const int32_t fstart = f1 < F ? __ldg(pos2 + f1) : p1;
-        if (p1 > (fstart > p0 ? fstart : p0)) {
-            const int32_t j = __ldg(crd1 + f1);
-            if (active) {
-                AT cv[EPL];
-                ld_vec<EPL>(C + (int64_t)j * ldc + col, cv);
-#pragma unroll
-                for (int q = 0; q < EPL; ++q) a[q] = fma(cv[q], t[q], a[q]);
-            }
             dirty = true;
+            a = bnd;
         }
-        const bool has = dirty && i < I;
-        if (lane == 0 && blockIdx.y == 0) carry_row[c] = has ? i : -1;
-        if (has && active) {
+    }
+    // slices cs .. s1-1 have their last fiber inside this piece
+    if (cs < s1) finish_to(s1);
+    // the piece may end inside slice s1: its partial is a binary64 carry
+    if (carry_row) {
+        const bool has = dirty && cs == s1 && s1 < I;
+        AT t[EPL];
+        warp_total(t);
+        if (lane == 0 && blockIdx.y == 0) carry_row[c] = has ? s1 : -1;
+        if (has && gi == 0 && active) {
 #pragma unroll
-            for (int q = 0; q < EPL; ++q) carry_val[c * R + col + q] = (double)a[q];
+            for (int e = 0; e < EPL; ++e) carry_val[c * R + col + e] = (double)t[e];
         }
     }
 }
 
-template <typename VT, int EPL>
-static spd_status launch_mttkrp_epl(const spd_csf3 *B, const void *C, int64_t ldc, const void *D, int64_t ldd,
-                                    int64_t R, void *A, int64_t lda, int split, const Tuning &tn, void *ws,
-                                    cudaStream_t st) {
+template <typename VT, int EPL, int G>
+static spd_status launch_mttkrp_g(const spd_csf3 *B, const void *C, int64_t ldc, const void *D, int64_t ldd,
+                                  int64_t R, void *A, int64_t lda, int split, const Tuning &tn, void *ws,
+                                  cudaStream_t st) {
     using OT = typename Traits<VT>::out;
-    constexpr int U = 8;
-    const int wpb = tn.block_threads / 32;
-    const int64_t ctiles = ceil_div(R, 32 * EPL);
+    const int threads = tn.block_threads > 256 ? 256 : tn.block_threads;  // shared windows for <= 8 warps
+    const int wpb = threads / 32;
+    const int64_t ctiles = ceil_div(R, G * EPL);
     const VT *v = static_cast<const VT *>(B->vals);
     const VT *cc = static_cast<const VT *>(C);
     const VT *dd = static_cast<const VT *>(D);
@@ -216,7 +207,7 @@ static spd_status launch_mttkrp_epl(const spd_csf3 *B, const void *C, int64_t ld
         if (P > B->dim0) P = B->dim0;
         if (P < 1) P = 1;
         dim3 grid((unsigned)ceil_div(P, wpb), (unsigned)ctiles);
-        spmttkrp_warp_kernel<VT, EPL, U><<<grid, tn.block_threads, 0, st>>>(
+        spmttkrp_warp_kernel<VT, EPL, G><<<grid, threads, 0, st>>>(
             B->dim0, B->nfib, B->pos1, B->crd1, B->pos2, B->crd2, v, cc, ldc, dd, ldd, R, aa, lda, nullptr, nullptr,
             nullptr, 0, P, nullptr, nullptr);
         return check_launch("spmttkrp_warp_kernel(row)");
@@ -234,25 +225,33 @@ static spd_status launch_mttkrp_epl(const spd_csf3 *B, const void *C, int64_t ld
                                                                                      Lw.npieces, psl);
     if ((s = check_launch("slice_partition_kernel"))) return s;
     dim3 grid((unsigned)ceil_div(Lw.npieces, wpb), (unsigned)ctiles);
-    spmttkrp_warp_kernel<VT, EPL, U><<<grid, tn.block_threads, 0, st>>>(
+    spmttkrp_warp_kernel<VT, EPL, G><<<grid, threads, 0, st>>>(
         B->dim0, B->nfib, B->pos1, B->crd1, B->pos2, B->crd2, v, cc, ldc, dd, ldd, R, aa, lda, pfib, ppos, psl,
         Lw.npieces, 0, crow, cval);
     if ((s = check_launch("spmttkrp_warp_kernel(nnz)"))) return s;
     return launch_carry_fixup<OT>(Lw.npieces, R, crow, cval, aa, lda, st);
 }
 
+template <typename VT, int EPL>
+static spd_status launch_mttkrp_epl(const spd_csf3 *B, const void *C, int64_t ldc, const void *D, int64_t ldd,
+                                    int64_t R, void *A, int64_t lda, int split, const Tuning &tn, void *ws,
+                                    cudaStream_t st) {
+    const int64_t lanes = ceil_div(R > 0 ? R : 1, EPL);
+    if (lanes <= 4) return launch_mttkrp_g<VT, EPL, 4>(B, C, ldc, D, ldd, R, A, lda, split, tn, ws, st);
+    if (lanes <= 8) return launch_mttkrp_g<VT, EPL, 8>(B, C, ldc, D, ldd, R, A, lda, split, tn, ws, st);
+    if (lanes <= 16) return launch_mttkrp_g<VT, EPL, 16>(B, C, ldc, D, ldd, R, A, lda, split, tn, ws, st);
+    return launch_mttkrp_g<VT, EPL, 32>(B, C, ldc, D, ldd, R, A, lda, split, tn, ws, st);
+}
+
 template <typename VT>
 static spd_status launch_mttkrp(const spd_csf3 *B, const void *C, int64_t ldc, const void *D, int64_t ldd, int64_t R,
                                 void *A, int64_t lda, int split, const Tuning &tn, void *ws, cudaStream_t st) {
     using OT = typename Traits<VT>::out;
-    int e1 = pick_epl(R, sizeof(VT), sizeof(OT), C, ldc, A, lda);
-    int e2 = pick_epl(R, sizeof(VT), sizeof(OT), D, ldd, A, lda);
-    int epl = e1 < e2 ? e1 : e2;
-    switch (epl) {
-        case 1: return launch_mttkrp_epl<VT, 1>(B, C, ldc, D, ldd, R, A, lda, split, tn, ws, st);
-        case 2: return launch_mttkrp_epl<VT, 2>(B, C, ldc, D, ldd, R, A, lda, split, tn, ws, st);
-        default: return launch_mttkrp_epl<VT, 4>(B, C, ldc, D, ldd, R, A, lda, split, tn, ws, st);
-    }
+    constexpr int V = 16 / sizeof(VT) < 16 / sizeof(OT) ? 16 / sizeof(VT) : 16 / sizeof(OT);  // one 16-byte vector
+    const bool vec = R % V == 0 && ldc % V == 0 && ldd % V == 0 && lda % V == 0 && aligned(C, 16) && aligned(D, 16) &&
+                     aligned(A, 16);
+    if (vec) return launch_mttkrp_epl<VT, V>(B, C, ldc, D, ldd, R, A, lda, split, tn, ws, st);
+    return launch_mttkrp_epl<VT, 1>(B, C, ldc, D, ldd, R, A, lda, split, tn, ws, st);
 }
 
 }  // namespace spd
