@@ -52,6 +52,8 @@ def parse_args(argv=None):
     p.add_argument("--no-variants", action="store_true", help="skip the per-variant table")
     p.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of CPU oracle work for cpu_baseline")
     p.add_argument("--e2e-steps", type=int, default=5)
+    p.add_argument("--fixed-tune", default="",
+                   help="UNIT,BLOCK,INFLIGHT: skip the autotuner and run SpMM with this tuning (nnz split)")
     p.add_argument("--rows", default="all",
                    help="comma list of extra hot-path rows to measure: cfg1,sddmm,backward,csf,batched (or all, none)")
     return p.parse_args(argv)
@@ -113,6 +115,41 @@ def algorithmic_bytes(kernel: str, n: int, nnz: int, vbytes: int, xbytes: int, y
     if kernel == "spmv":
         return base + xbytes * n + ybytes * n
     return base + xbytes * n * L + ybytes * n * L
+
+
+SPMM_SOURCES = ("paper_2207_13901_gb300/csrc/spd_spmm.cu", "paper_2207_13901_gb300/csrc/spd_spmm_piece.cuh",
+                "paper_2207_13901_gb300/csrc/spd_internal.cuh", "paper_2207_13901_gb300/csrc/spd_core.cu")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_spmm_rmat22_f32.md")
+
+
+def spmm_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for rel in SPMM_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(tune):
+    """DRAM bytes per SpMM call from the committed ncu summary, if it was taken on the
+    current kernel sources with the same tuning; otherwise None."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    vals = {}
+    with open(TRAFFIC_FILE) as f:
+        for line in f:
+            if ":" in line and line.strip().startswith("- "):
+                k, v = line.strip()[2:].split(":", 1)
+                vals[k.strip()] = v.strip().strip("`")
+    try:
+        if vals.get("source_hash") != spmm_source_hash():
+            return None
+        if vals.get("tune") != "%d,%d,%d" % (tune["unit_items"], tune["block_threads"], tune.get("inflight", 8)):
+            return None
+        return int(vals["dram_bytes_per_spmm_call"])
+    except (KeyError, ValueError, TypeError):
+        return None
 
 
 def measured_peaks():
@@ -227,10 +264,16 @@ def run_gpu(args):
     from paper_2207_13901_gb300.autotune import Autotuner
     import tempfile
     tuner = Autotuner(path=os.path.join(tempfile.mkdtemp(prefix="spd_tune_"), "autotune.json"))
-    best_spmm = tuner.spmm(Ad, Xd, Y, force=True)
-    spmm_table = tuner.last_table
-    best_spmv = tuner.spmv(Ad, xd, y, force=True)
-    spmv_table = tuner.last_table
+    if args.fixed_tune:
+        u, bt, inf = (int(v) for v in args.fixed_tune.split(","))
+        best_spmm = {"split": "nnz", "tune": {"unit_items": u, "block_threads": bt, "inflight": inf}}
+        best_spmv = {"split": "nnz", "tune": None}
+        spmm_table = spmv_table = "fixed"
+    else:
+        best_spmm = tuner.spmm(Ad, Xd, Y, force=True)
+        spmm_table = tuner.last_table
+        best_spmv = tuner.spmv(Ad, xd, y, force=True)
+        spmv_table = tuner.last_table
     sp_v, tu_v = best_spmv["split"], best_spmv["tune"]
     sp_m, tu_m = best_spmm["split"], best_spmm["tune"]
 
@@ -451,7 +494,9 @@ def run_gpu(args):
                 "peak_kind": peak_kind,
                 "unit": "GB/s",
                 "frac": round(spmm_gbs / hbm, 4),
-                "traffic": None,
+                "traffic": recorded_traffic(tu_m) if (sp_m == "nnz" and tu_m) else None,
+                "traffic_source": "profiles/traffic_spmm_rmat22_f32.md (ncu dram__bytes_read.sum + dram__bytes_write.sum "
+                                  "of the partition, warp and fix-up kernels of one call)",
                 "algorithmic_bytes": spmm_bytes,
                 "spmv_achieved": round(spmv_bytes / (spmv_ms * 1e-3) / 1e9, 1),
                 "spmv_frac": round(spmv_bytes / (spmv_ms * 1e-3) / 1e9 / hbm, 4),
