@@ -630,7 +630,9 @@ def row_sddmm(hbm):
 
 def row_backward(A, X32, hbm):
     """SpMM backward on the 2^22 R-MAT with L = 128 in binary32: dvals = SDDMM(pattern,
-    dY, X) and dX = SpMM^T(A, dY) (torch.autograd through the hand-written backward)."""
+    dY, X) and dX = SpMM^T(A, dY) (torch.autograd through the hand-written backward; dX
+    as an SpMM over A^T, whose structure is built once per pattern, and, for
+    comparison, by atomic scatter)."""
     import torch
     import oracle
     import paper_2207_13901_gb300 as spd
@@ -648,14 +650,19 @@ def row_backward(A, X32, hbm):
         Y = spd.autograd.spmm(pattern.with_vals(vals), Xd)
         Y.backward(W)
 
-    ms_all = _time_ms(fwd_bwd, reps=3, warm=1)
+    ms_transpose = _time_ms(lambda: spd.transpose(dA), reps=3, warm=1)  # once per pattern
+    ms_all = _time_ms(fwd_bwd, reps=3, warm=1)  # dX over the cached A^T
     ms_sddmm = _time_ms(lambda: spd.sddmm(pattern, W, Xd.detach()), reps=3, warm=1)
     ms_spmmt = _time_ms(lambda: spd.spmm_t(dA, W), reps=3, warm=1)
+    ms_spmmt_tr = _time_ms(lambda: spd.spmm_t(dA, W, method="transpose"), reps=3, warm=1)
     b_sddmm = 4 * (n + 1) + 8 * nnz + 4 * 2 * n * L
     b_spmmt = 4 * (n + 1) + 8 * nnz + 4 * n * L + 4 * n * L
+    b_spmmt_tr = b_spmmt + 12 * nnz  # plus the value gather into A^T's order
     out = {"forward_backward_ms": round(ms_all, 3),
+           "transpose_build_ms": round(ms_transpose, 3),
            "sddmm_dvals": _entry(ms_sddmm, nnz, b_sddmm, hbm),
-           "spmm_t_dX": _entry(ms_spmmt, nnz, b_spmmt, hbm)}
+           "spmm_t_dX_atomic": _entry(ms_spmmt, nnz, b_spmmt, hbm),
+           "spmm_t_dX_transpose": _entry(ms_spmmt_tr, nnz, b_spmmt_tr, hbm)}
     rng = np.random.default_rng(1)
     sel = np.unique(rng.integers(0, nnz, 2000))
     Wh = W.cpu().numpy().astype(np.float64)
@@ -663,6 +670,14 @@ def row_backward(A, X32, hbm):
     ref = oracle.sddmm(A.pos, A.crd, None, Wh, X32.astype(np.float64), sel=sel, accurate=True)
     sc = oracle.sddmm(A.pos, A.crd, None, np.abs(Wh), np.abs(X32.astype(np.float64)), sel=sel)
     out["sddmm_dvals"]["error"] = error_stats(gv[sel], ref, sc)
+    # dX rows j of A^T W, from the oracle's own transposition of A
+    t_pos, t_crd, perm = oracle.csr_transpose(A.pos, A.crd, n)
+    jsel = np.unique(np.concatenate([rng.integers(0, n, 600), np.argsort(np.diff(t_pos))[-5:]]))
+    vr = A.vals.astype(np.float32).astype(np.float64)[perm]
+    ref = oracle.spmm(t_pos, t_crd, vr, Wh, sel=jsel, accurate=True)
+    sc = oracle.spmm(t_pos, t_crd, np.abs(vr), np.abs(Wh), sel=jsel)
+    gx = Xd.grad.double().cpu().numpy()[jsel]
+    out["spmm_t_dX_transpose"]["error"] = error_stats(gx, ref, sc)
     del dA, vals, Xd, W
     torch.cuda.empty_cache()
     return out

@@ -207,6 +207,37 @@ spd_status spd_spmm_t(const spd_csr *A, const void *dY, int64_t L, int64_t ldy, 
                       void *dX, int64_t ldx, int dx_type, int split, const spd_tune *tune,
                       void *ws, size_t ws_bytes, void *stream);
 
+/* -------------------------------------------------------------------- transposed schedule
+ *
+ * A^T in the same {Dense, Compressed} level formats, i.e. A in the CSC encoding (the
+ * format language of Section II-B: the level formats of CSR with the dimension order
+ * reversed). With it, the SpMM gradient dX = A^T dY is an ordinary spd_spmm over
+ * (t_pos, t_crd, gathered values): every row of dX is written once, in a fixed order,
+ * with no atomic scatter. The paper's statements do not need it; the structure depends
+ * only on A's pattern, so a caller computes it once and reuses it while only the values
+ * change. */
+
+/* Workspace bytes of spd_csr_transpose (host only): about 12 bytes per nonzero plus
+ * 1 KiB per 4096 nonzeros. */
+spd_status spd_csr_transpose_workspace_size(const spd_csr *A, size_t *bytes);
+
+/* The structure of A^T (ncols x nrows) and the permutation into it, all device int32:
+ *   t_pos[ncols + 1]: t_pos[j] = number of entries of A in columns < j;
+ *   t_crd[nnz]: row coordinates, ascending within each column (entries of a column
+ *               keep A's row order: a stable sort of A's positions by column);
+ *   perm[nnz]: perm[q] = the position in A of the q-th entry of A^T, so that A^T's
+ *              values are vals[perm[q]] (spd_gather_vals).
+ * A->vals is not read. Caller-owned outputs; ws of spd_csr_transpose_workspace_size
+ * bytes, 256-byte aligned. Asynchronous on `stream`; the result is deterministic.
+ * A's structure must be valid (spd_csr_validate): coordinates outside [0, ncols) give
+ * an unspecified (but in-bounds) result. */
+spd_status spd_csr_transpose(const spd_csr *A, int32_t *t_pos, int32_t *t_crd, int32_t *perm, void *ws,
+                             size_t ws_bytes, void *stream);
+
+/* out[q] = in[perm[q]] for q < n: n elements of vtype, device memory, caller-owned.
+ * Carries A's values into A^T's order. Asynchronous. */
+spd_status spd_gather_vals(int64_t n, const int32_t *perm, const void *in, void *out, int vtype, void *stream);
+
 /* SDDMM A(i,j) = B(i,j) * C(i,k) * D(k,j), k < K. The output keeps B's pattern
  * (Section V-B): out_vals[p] is the value at B's position p, and B's pos/crd serve as
  * the output's. B->vals may be NULL: every B value is then 1 (the sampling pattern).

@@ -61,6 +61,7 @@ _SIGS = {
     "orc_spmttkrp": [_I64, _I64, _P, _P, _P, _P, _P, _P, _I64, _P, _I64, _I64, _P, _P, _I64],
     "orc_spmttkrp_acc": [_I64, _I64, _P, _P, _P, _P, _P, _P, _I64, _P, _I64, _I64, _P, _P, _I64],
     "orc_validate_level": [_I64, _I64, _P, _P, _I64, _P],
+    "orc_csr_transpose": [_I64, _I64, _P, _P, _P, _P, _P],
 }
 
 
@@ -127,6 +128,18 @@ def pos_split(pos, positions) -> np.ndarray:
     rows = np.zeros(q.shape[0], dtype=np.int64)
     lib().orc_pos_split(pos.shape[0] - 1, _ptr(pos), q.shape[0], _ptr(q), _ptr(rows))
     return rows
+
+
+def csr_transpose(pos, crd, ncols: int):
+    """A^T's structure (t_pos, t_crd) and perm, perm[q] = A's position of A^T's entry q."""
+    pos = _i32(pos)
+    crd = _i32(crd)
+    nnz = crd.shape[0]
+    t_pos = np.zeros(ncols + 1, dtype=np.int32)
+    t_crd = np.zeros(nnz, dtype=np.int32)
+    perm = np.zeros(nnz, dtype=np.int32)
+    lib().orc_csr_transpose(pos.shape[0] - 1, ncols, _ptr(pos), _ptr(crd), _ptr(t_pos), _ptr(t_crd), _ptr(perm))
+    return t_pos, t_crd, perm
 
 
 def validate_level(nparent: int, nchild_dim: int, pos, crd):

@@ -408,3 +408,28 @@ int64_t orc_validate_level(int64_t nparent, int64_t nchild_dim, const int32_t *p
         }
     return bad;
 }
+
+/* ------------------------------------------------------------------------------------
+ * Transposed structure: A^T in the same {Dense, Compressed} level formats (the CSC
+ * encoding of A; Section II-B: CSR's level formats with the dimension order reversed).
+ * A counting sort by column that walks A in ascending position order, so the entries
+ * of each column keep A's row order.
+ *   t_pos[j]  = number of entries of A in columns < j   (ncols + 1 entries)
+ *   t_crd[q]  = row of the q-th entry of A^T
+ *   perm[q]   = position in A of the q-th entry of A^T
+ * ------------------------------------------------------------------------------------ */
+void orc_csr_transpose(int64_t n, int64_t ncols, const int32_t *pos, const int32_t *crd,
+                       int32_t *t_pos, int32_t *t_crd, int32_t *perm) {
+    int64_t *next = (int64_t *)calloc((size_t)(ncols > 0 ? ncols : 1), sizeof(int64_t));
+    for (int64_t j = 0; j <= ncols; ++j) t_pos[j] = 0;
+    for (int64_t p = 0; p < pos[n]; ++p) t_pos[crd[p] + 1] += 1;   /* column counts */
+    for (int64_t j = 0; j < ncols; ++j) t_pos[j + 1] += t_pos[j];  /* running totals */
+    for (int64_t j = 0; j < ncols; ++j) next[j] = t_pos[j];
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t p = pos[i]; p < pos[i + 1]; ++p) {
+            const int64_t q = next[crd[p]]++;
+            t_crd[q] = (int32_t)i;
+            perm[q] = (int32_t)p;
+        }
+    free(next);
+}

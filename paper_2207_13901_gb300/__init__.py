@@ -5,10 +5,11 @@ SpMV, SpMM, SpMM^T, SDDMM, SpTTV and SpMTTKRP over CSR {Dense, Compressed} and C
 nonzeros (coordinate fusion + non-zero partition), executed by hand-written sm_103a
 kernels behind the C ABI of include/spd.h. PyTorch supplies memory and streams.
 """
-from .ops import (CSF3, CSR, csf3_workspace_size, csr_workspace_size, partition, result_dtype, sddmm, spmm, spmm_t,
-                  spmttkrp, spmv, spttv, validate)
+from .ops import (CSF3, CSR, CSRTranspose, csf3_workspace_size, csr_workspace_size, gather_vals, partition,
+                  result_dtype, sddmm, spmm, spmm_t, spmttkrp, spmv, spttv, transpose, validate)
 from . import autograd, batched
 from .batched import SpMMBatch
 
-__all__ = ["CSR", "CSF3", "spmv", "spmm", "spmm_t", "sddmm", "spttv", "spmttkrp", "validate", "partition",
+__all__ = ["CSR", "CSF3", "CSRTranspose", "spmv", "spmm", "spmm_t", "sddmm", "spttv", "spmttkrp", "validate",
+           "partition", "transpose", "gather_vals",
            "csr_workspace_size", "csf3_workspace_size", "result_dtype", "autograd", "batched", "SpMMBatch"]

@@ -89,6 +89,9 @@ SIGNATURES = {
     "spd_spmv": (_I, [_CSR, _P, _I, _P, _I, _I, _TUNE, _P, _SZ, _P]),
     "spd_spmm": (_I, [_CSR, _P, _I64, _I64, _I, _P, _I64, _I, _I, _TUNE, _P, _SZ, _P]),
     "spd_spmm_t": (_I, [_CSR, _P, _I64, _I64, _I, _P, _I64, _I, _I, _TUNE, _P, _SZ, _P]),
+    "spd_csr_transpose_workspace_size": (_I, [_CSR, ctypes.POINTER(ctypes.c_size_t)]),
+    "spd_csr_transpose": (_I, [_CSR, _P, _P, _P, _P, _SZ, _P]),
+    "spd_gather_vals": (_I, [_I64, _P, _P, _P, _I, _P]),
     "spd_sddmm": (_I, [_CSR, _P, _I64, _I64, _P, _I64, _I, _P, _I, _I, _TUNE, _P, _SZ, _P]),
     "spd_spttv": (_I, [_CSF, _P, _I, _P, _I, _I, _TUNE, _P, _SZ, _P]),
     "spd_spmttkrp": (_I, [_CSF, _P, _I64, _P, _I64, _I64, _I, _P, _I64, _I, _I, _TUNE, _P, _SZ, _P]),

@@ -43,7 +43,7 @@ __device__ __forceinline__ int64_t batch_of(const int64_t *__restrict__ pstart, 
 }
 
 template <typename VT, int EPL, int U, bool FULLTILE>
-__global__ void __launch_bounds__(256) spmm_batched_kernel(const BatchDesc *__restrict__ descs,
+__global__ void __launch_bounds__(256, kSpmmMinBlocks) spmm_batched_kernel(const BatchDesc *__restrict__ descs,
                                                            const int64_t *__restrict__ pstart, int64_t count,
                                                            int64_t total, int64_t L, const int32_t *__restrict__ prow,
                                                            const int32_t *__restrict__ ppos, int32_t *carry_row,

@@ -15,14 +15,8 @@ namespace spd {
 
 constexpr unsigned FULL = kFullMask;
 
-// Blocks of 256 threads per SM the SpMM kernel must fit: 4 caps it at 64 registers, so
-// 32 warps (of 128-thread blocks) stay resident to keep enough rows of X in flight.
-#ifndef SPMM_MIN_BLOCKS
-#define SPMM_MIN_BLOCKS 4
-#endif
-
 template <typename VT, int EPL, int U, bool FULLTILE>
-__global__ void __launch_bounds__(256, SPMM_MIN_BLOCKS) spmm_warp_kernel(
+__global__ void __launch_bounds__(256, kSpmmMinBlocks) spmm_warp_kernel(
     int64_t n, const int32_t *__restrict__ pos, const int32_t *__restrict__ crd, const VT *__restrict__ vals,
     const VT *__restrict__ X, uint32_t ldx_bytes, typename Traits<VT>::out *__restrict__ Y, int64_t ldy, int64_t L,
     const int32_t *__restrict__ prow, const int32_t *__restrict__ ppos, int64_t npieces, int64_t P,

@@ -17,6 +17,10 @@ namespace spd {
 constexpr unsigned kFullMask = 0xffffffffu;
 constexpr int32_t kLongRow = 4096;
 
+// Blocks of 256 threads per SM the SpMM kernels must fit: 4 caps them at 64 registers,
+// so 32 warps stay resident to keep enough rows of X in flight.
+constexpr int kSpmmMinBlocks = 4;
+
 template <typename T, int N>
 __device__ __forceinline__ void zero(T (&a)[N]) {
 #pragma unroll

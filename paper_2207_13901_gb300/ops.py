@@ -67,7 +67,11 @@ def _tune(tune) -> Optional[ctypes.POINTER(_abi.spd_tune)]:
 class CSR:
     """A device CSR matrix: pos int32[nrows+1], crd int32[nnz], vals[nnz]."""
 
-    def __init__(self, pos: torch.Tensor, crd: torch.Tensor, vals: Optional[torch.Tensor], shape: Tuple[int, int]):
+    def __init__(self, pos: torch.Tensor, crd: torch.Tensor, vals: Optional[torch.Tensor], shape: Tuple[int, int],
+                 _structure_cache: Optional[dict] = None):
+        # results that depend only on the pattern (the transposed structure), shared by
+        # every matrix made from this one with with_vals
+        self._structure_cache = {} if _structure_cache is None else _structure_cache
         self.pos = _cuda(pos, "pos")
         self.crd = _cuda(crd, "crd")
         self.vals = vals if vals is None else _cuda(vals, "vals")
@@ -91,7 +95,15 @@ class CSR:
         return self.vals.dtype if self.vals is not None else torch.float32
 
     def with_vals(self, vals: Optional[torch.Tensor]) -> "CSR":
-        return CSR(self.pos, self.crd, vals, self.shape)
+        return CSR(self.pos, self.crd, vals, self.shape, self._structure_cache)
+
+    def transposed(self, stream=None) -> "CSRTranspose":
+        """A^T's structure (computed once per pattern, then reused)."""
+        t = self._structure_cache.get("transpose")
+        if t is None:
+            t = transpose(self, stream=stream)
+            self._structure_cache["transpose"] = t
+        return t
 
     def desc(self, vtype: Optional[torch.dtype] = None) -> _abi.spd_csr:
         vt = vtype if vtype is not None else self.dtype
@@ -146,6 +158,21 @@ class CSF3:
         t = lambda a: torch.as_tensor(a).to(device=device, dtype=torch.int32).contiguous()
         v = torch.as_tensor(vals).to(dtype=dtype).to(device).contiguous()
         return cls(t(pos1), t(crd1), t(pos2), t(crd2), v, dims)
+
+
+class CSRTranspose:
+    """The structure of A^T for a fixed pattern of A (``spd_csr_transpose``): t_pos
+    int32[ncols+1], t_crd int32[nnz] (row coordinates, ascending in each column) and
+    perm int32[nnz] (A's position of each entry of A^T)."""
+
+    def __init__(self, t_pos: torch.Tensor, t_crd: torch.Tensor, perm: torch.Tensor, shape: Tuple[int, int]):
+        self.t_pos, self.t_crd, self.perm = t_pos, t_crd, perm
+        self.shape = shape  # A's shape
+
+    def matrix(self, vals: Optional[torch.Tensor], stream=None) -> CSR:
+        """A^T as a CSR matrix (ncols x nrows) carrying ``vals`` (A's values, A's order)."""
+        tv = None if vals is None else gather_vals(self.perm, vals, stream=stream)
+        return CSR(self.t_pos, self.t_crd, tv, (self.shape[1], self.shape[0]))
 
 
 # ---------------------------------------------------------------------------- workspace
@@ -271,13 +298,23 @@ def spmm(A: CSR, X: torch.Tensor, Y: Optional[torch.Tensor] = None, split="nnz",
 
 
 def spmm_t(A: CSR, dY: torch.Tensor, dX: Optional[torch.Tensor] = None, split="nnz", tune=None, ws=None,
-           stream=None):
-    """dX(j,l) = A(i,j) dY(i,l): the gradient of Y = A X with respect to X."""
+           stream=None, method: str = "atomic"):
+    """dX(j,l) = A(i,j) dY(i,l): the gradient of Y = A X with respect to X.
+
+    method="atomic": walk A's rows and scatter into dX with atomic adds (no extra
+    memory; summation order not deterministic). method="transpose": SpMM over A^T,
+    whose structure is computed once per pattern (``CSR.transposed``); each row of dX is
+    written once in a fixed order, so the result is deterministic."""
     lib = _abi.load()
     _cuda(dY, "dY")
     n, m = A.shape
     if dY.dim() != 2 or dY.shape[0] != n or dY.dtype != A.dtype or dY.stride(1) != 1:
         raise ValueError("dY must be a row-major %d x L matrix of %s" % (n, A.dtype))
+    if method == "transpose":
+        At = A.transposed(stream=stream).matrix(A.vals, stream=stream)
+        return spmm(At, dY, Y=dX, split=split, tune=tune, ws=ws, stream=stream)
+    if method != "atomic":
+        raise ValueError("method must be 'atomic' or 'transpose'")
     L = dY.shape[1]
     if dX is None:
         dX = torch.empty((m, L), dtype=result_dtype(A.dtype), device=dY.device)
@@ -289,6 +326,38 @@ def spmm_t(A: CSR, dY: torch.Tensor, dX: Optional[torch.Tensor] = None, split="n
                                             dX.stride(0), _code(dX.dtype), _split(split), _tune(tune), _ptr(buf), nb,
                                             st))
     return dX
+
+
+def transpose(A: CSR, stream=None, ws=None) -> CSRTranspose:
+    """The structure of A^T and the permutation into it (deterministic)."""
+    lib = _abi.load()
+    n, m = A.shape
+    dev = A.pos.device
+    st = _stream(stream)
+    d = A.desc()
+    nb = ctypes.c_size_t(0)
+    _abi.check("spd_csr_transpose_workspace_size", lib.spd_csr_transpose_workspace_size(ctypes.byref(d), ctypes.byref(nb)))
+    buf, nbytes = _ws(int(nb.value), dev, st, ws)
+    t_pos = torch.empty(m + 1, dtype=torch.int32, device=dev)
+    t_crd = torch.empty(A.nnz, dtype=torch.int32, device=dev)
+    perm = torch.empty(A.nnz, dtype=torch.int32, device=dev)
+    _abi.check("spd_csr_transpose", lib.spd_csr_transpose(ctypes.byref(d), _ptr(t_pos), _ptr(t_crd), _ptr(perm),
+                                                          _ptr(buf), nbytes, st))
+    return CSRTranspose(t_pos, t_crd, perm, A.shape)
+
+
+def gather_vals(perm: torch.Tensor, vals: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None):
+    """out[q] = vals[perm[q]] (A's values in A^T's order)."""
+    lib = _abi.load()
+    _cuda(perm, "perm")
+    _cuda(vals, "vals")
+    if perm.dtype != torch.int32 or not perm.is_contiguous() or not vals.is_contiguous():
+        raise ValueError("perm must be contiguous int32 and vals contiguous")
+    if out is None:
+        out = torch.empty(perm.numel(), dtype=vals.dtype, device=vals.device)
+    _abi.check("spd_gather_vals", lib.spd_gather_vals(perm.numel(), _ptr(perm), _ptr(vals), _ptr(out),
+                                                      _code(vals.dtype), _stream(stream)))
+    return out
 
 
 def sddmm(B: CSR, C: torch.Tensor, Dnk: torch.Tensor, out: Optional[torch.Tensor] = None, split="nnz", tune=None,

@@ -93,6 +93,24 @@ def test_workspace_sizes():
     assert size.value > 0
 
 
+def test_transpose_host_checks():
+    lib = _abi.load()
+    size = ctypes.c_size_t(0)
+    A = _csr(nrows=1000, ncols=1000, nnz=20000)
+    assert lib.spd_csr_transpose_workspace_size(ctypes.byref(A), ctypes.byref(size)) == 0
+    assert size.value >= 3 * 4 * 20000 + 256 * 4 * (-(-20000 // 4096))  # keys x2, payload, digit counts
+    assert lib.spd_csr_transpose_workspace_size(ctypes.byref(A), None) == 1
+    # NULL outputs, short workspace, misaligned outputs: refused before any launch
+    assert lib.spd_csr_transpose(ctypes.byref(A), None, 4096, 8192, 1 << 20, 1 << 30, None) == 1
+    assert lib.spd_csr_transpose(ctypes.byref(A), 4096, 8192, 12288, 1 << 20, 16, None) == 6
+    assert lib.spd_csr_transpose(ctypes.byref(A), 4098, 8192, 12288, 1 << 20, 1 << 30, None) == 4
+    assert lib.spd_gather_vals(-1, 256, 512, 1024, _abi.SPD_F32, None) == 2
+    assert lib.spd_gather_vals(10, 256, 512, 1024, 9, None) == 3
+    assert lib.spd_gather_vals(10, None, 512, 1024, _abi.SPD_F32, None) == 1
+    assert lib.spd_gather_vals(10, 256, 514, 1024, _abi.SPD_F32, None) == 4
+    assert lib.spd_gather_vals(0, None, None, None, _abi.SPD_F32, None) == 0  # nothing to do
+
+
 def test_product_path_has_no_oracle_dependency():
     """The package never imports or loads the oracle (no CPU fallback)."""
     pkg = os.path.join(ROOT, "paper_2207_13901_gb300")

@@ -47,7 +47,7 @@ def check_batch(mats, Xs, Ys, dtype):
 
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16, torch.float64])
-@pytest.mark.parametrize("L", [64, 7])
+@pytest.mark.parametrize("L", [64, 16, 7])
 def test_batched_policies(dtype, L):
     mats = make_batch(1)
     rng = np.random.default_rng(2)

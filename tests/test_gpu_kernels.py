@@ -176,8 +176,10 @@ def test_spmv_split_invariance_integer_exact(dtype):
 
 @pytest.mark.parametrize("name", ["uniform4096", "rmat12", "longrow", "col0", "empty_rows", "no_nnz"])
 @pytest.mark.parametrize("dtype", DTYPES)
-@pytest.mark.parametrize("L", [1, 7, 64, 128])
+@pytest.mark.parametrize("L", [1, 7, 16, 32, 48, 64, 128])
 def test_spmm(name, dtype, L):
+    """L picks the lane shape: vector lanes covering whole tiles (64, 128), narrower
+    vectors with idle lanes (16, 32, 48) and scalar lanes (1, 7)."""
     A = get_mats()[name]
     rng = np.random.default_rng(12)
     X = rng.uniform(-1, 1, (A.ncols, L))

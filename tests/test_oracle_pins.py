@@ -85,6 +85,15 @@ def test_golden_partitions():
     assert np.array_equal(oracle.row_split(4, int(g["pieces"][0])), g["row_bounds"])
 
 
+def test_golden_transpose():
+    g = read_golden("transpose_4x5.txt")
+    t_pos, t_crd, perm = oracle.csr_transpose(g["pos"], g["crd"], int(g["ncols"][0]))
+    assert np.array_equal(t_pos, g["t_pos"])
+    assert np.array_equal(t_crd, g["t_crd"])
+    assert np.array_equal(perm, g["perm"])
+    assert np.array_equal(g["vals"][perm], g["t_vals"])
+
+
 # ------------------------------------------------------------------------------ dense brute force
 
 @pytest.mark.parametrize("seed", SEEDS)
@@ -370,6 +379,46 @@ def test_validate_level_detects_planted_faults():
     crd[3] = 20
     cnt, first = oracle.validate_level(30, 20, A.pos, crd)
     assert cnt == 1 and first == 31 + 3
+
+
+# ------------------------------------------------------------------------------ transposed structure
+
+@pytest.mark.parametrize("seed", SEEDS)
+def test_transpose_dense_and_involution(seed):
+    """A^T built from (t_pos, t_crd, vals[perm]) equals the dense transpose; transposing
+    twice gives A back and the two permutations compose to the identity."""
+    rng = np.random.default_rng(seed)
+    A = small_csr(rng, 37, 23, 0.15, long_rows=1, integer=True)
+    t_pos, t_crd, perm = oracle.csr_transpose(A.pos, A.crd, A.ncols)
+    At = spd_synth.CSR(A.ncols, A.nrows, t_pos, t_crd, A.vals[perm])
+    assert np.array_equal(dense_of_csr(At), dense_of_csr(A).T)
+    assert np.array_equal(np.sort(perm), np.arange(A.nnz))
+    b_pos, b_crd, perm2 = oracle.csr_transpose(t_pos, t_crd, A.nrows)
+    assert np.array_equal(b_pos, A.pos) and np.array_equal(b_crd, A.crd)
+    assert np.array_equal(perm[perm2], np.arange(A.nnz))
+
+
+def test_transpose_is_the_stable_sort_by_column():
+    """perm is numpy's stable sort of A's positions by column (rows ascending within a
+    column) and t_crd is sorted within every column."""
+    A = spd_synth.rmat_csr(11, 8, seed=4)
+    t_pos, t_crd, perm = oracle.csr_transpose(A.pos, A.crd, A.ncols)
+    assert np.array_equal(perm, np.argsort(A.crd, kind="stable"))
+    assert np.array_equal(t_pos, np.concatenate([[0], np.cumsum(np.bincount(A.crd, minlength=A.ncols))]))
+    rows = np.repeat(np.arange(A.nrows), np.diff(A.pos))
+    assert np.array_equal(t_crd, rows[perm])
+    seg = np.repeat(np.arange(A.ncols), np.diff(t_pos))
+    assert np.all((np.diff(t_crd) > 0) | (np.diff(seg) != 0))
+
+
+def test_transpose_against_scipy_csc():
+    sp = pytest.importorskip("scipy.sparse")
+    A = spd_synth.rmat_csr(10, 8, seed=6)
+    S = sp.csr_matrix((A.vals, A.crd, A.pos), shape=(A.nrows, A.ncols)).tocsc()
+    S.sort_indices()
+    t_pos, t_crd, perm = oracle.csr_transpose(A.pos, A.crd, A.ncols)
+    assert np.array_equal(t_pos, S.indptr) and np.array_equal(t_crd, S.indices)
+    assert np.array_equal(A.vals[perm], S.data)
 
 
 # ------------------------------------------------------------------------------ library cross-check
