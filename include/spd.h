@@ -125,12 +125,18 @@ typedef struct {
  *   block_threads threads per block for the warp-per-unit kernels: 64..1024,
  *                 multiple of 32.
  *   inflight      dense rows a warp keeps in flight per group in SpMM (4 or 8;
- *                 binary64 always uses 4). */
+ *                 binary64 always uses 4).
+ *   lane_groups   lane shape of SpMM when L < 32 vectors of 16 bytes: 1 = groups of
+ *                 4, 8 or 16 lanes, one 16-byte vector each, taking different nonzeros
+ *                 side by side; 2 = one nonzero per warp step over 32 narrower lanes;
+ *                 0 = the library's choice (groups when X is at most 64 MiB, so that its
+ *                 rows stay in L2 and the gathers are bound by instruction issue). */
 typedef struct {
     int32_t unit_items;
     int32_t row_pieces;
     int32_t block_threads;
     int32_t inflight;
+    int32_t lane_groups;
 } spd_tune;
 
 /* -------------------------------------------------------------------- misc */
@@ -280,7 +286,7 @@ typedef struct {
  * It points into the caller's workspace, which must outlive every run of the plan. */
 typedef struct {
     int64_t count, total_pieces, L;
-    int32_t vtype, epl, block_threads, grid, fulltile, has_nnz;
+    int32_t vtype, epl, group, block_threads, grid, fulltile, has_nnz;
     void *ws;
     size_t off_desc, off_pstart, off_prow, off_ppos, off_crow, off_cval;
 } spd_batch_plan;

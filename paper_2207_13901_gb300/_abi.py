@@ -46,7 +46,7 @@ class spd_csf3(ctypes.Structure):
 class spd_tune(ctypes.Structure):
     _fields_ = [
         ("unit_items", ctypes.c_int32), ("row_pieces", ctypes.c_int32),
-        ("block_threads", ctypes.c_int32), ("inflight", ctypes.c_int32),
+        ("block_threads", ctypes.c_int32), ("inflight", ctypes.c_int32), ("lane_groups", ctypes.c_int32),
     ]
 
 
@@ -60,7 +60,8 @@ class spd_batch_item(ctypes.Structure):
 class spd_batch_plan(ctypes.Structure):
     _fields_ = [
         ("count", ctypes.c_int64), ("total_pieces", ctypes.c_int64), ("L", ctypes.c_int64),
-        ("vtype", ctypes.c_int32), ("epl", ctypes.c_int32), ("block_threads", ctypes.c_int32),
+        ("vtype", ctypes.c_int32), ("epl", ctypes.c_int32), ("group", ctypes.c_int32),
+        ("block_threads", ctypes.c_int32),
         ("grid", ctypes.c_int32), ("fulltile", ctypes.c_int32), ("has_nnz", ctypes.c_int32),
         ("ws", ctypes.c_void_p),
         ("off_desc", ctypes.c_size_t), ("off_pstart", ctypes.c_size_t), ("off_prow", ctypes.c_size_t),

@@ -2,7 +2,7 @@
 
 For a shape class -- (operation, element type, log2 buckets of rows, nonzeros and the
 longest row, dense width, device name) -- every candidate setting (row vs nnz split,
-items per work unit, threads per block, rows in flight) is timed with CUDA events on the
+items per work unit, threads per block, rows in flight, SpMM lane shape) is timed with CUDA events on the
 caller's operands, and the fastest is kept in a JSON cache (``SPD_AUTOTUNE_CACHE``, by
 default ``~/.cache/spd/autotune.json``). Timing runs the real kernels through the C ABI
 outside any timed region of the caller; it reads the longest row once with a device
@@ -117,9 +117,14 @@ class Autotuner:
     def spmm(self, A: "ops.CSR", X: torch.Tensor, Y: Optional[torch.Tensor] = None, force: bool = False) -> dict:
         Y = Y if Y is not None else torch.empty((A.shape[0], X.shape[1]), dtype=ops.result_dtype(A.dtype), device=X.device)
         key = self.shape_key("spmm", A, X.shape[1], A.dtype)
-        include_row = True
-        return self.choose(key, warp_candidates(include_row, inflight=A.dtype != torch.float64),
-                           lambda c: (lambda: ops.spmm(A, X, Y, split=c["split"], tune=c["tune"])), force)
+        cands = warp_candidates(True, inflight=A.dtype != torch.float64)
+        if X.shape[1] * X.element_size() < 32 * 16:
+            # narrow L: both lane shapes (32 narrow lanes, or groups of 16-byte lanes)
+            for c in list(cands):
+                if c["tune"] is not None:
+                    for g in (1, 2):
+                        cands.append({"split": c["split"], "tune": dict(c["tune"], lane_groups=g)})
+        return self.choose(key, cands, lambda c: (lambda: ops.spmm(A, X, Y, split=c["split"], tune=c["tune"])), force)
 
     def spmv(self, A: "ops.CSR", x: torch.Tensor, y: Optional[torch.Tensor] = None, force: bool = False) -> dict:
         y = y if y is not None else torch.empty(A.shape[0], dtype=ops.result_dtype(A.dtype), device=x.device)

@@ -42,7 +42,7 @@ __device__ __forceinline__ int64_t batch_of(const int64_t *__restrict__ pstart, 
     return lo;
 }
 
-template <typename VT, int EPL, int U, bool FULLTILE>
+template <typename VT, int EPL, int G, bool FULLTILE>
 __global__ void __launch_bounds__(256, kSpmmMinBlocks) spmm_batched_kernel(const BatchDesc *__restrict__ descs,
                                                            const int64_t *__restrict__ pstart, int64_t count,
                                                            int64_t total, int64_t L, const int32_t *__restrict__ prow,
@@ -55,9 +55,10 @@ __global__ void __launch_bounds__(256, kSpmmMinBlocks) spmm_batched_kernel(const
     const int wid = threadIdx.x >> 5;
     const int64_t wpb = blockDim.x >> 5;
     const int64_t nwarps = (int64_t)gridDim.x * wpb;
-    const int64_t col = (int64_t)blockIdx.y * (32 * EPL) + (int64_t)lane * EPL;
+    const int64_t col = (int64_t)blockIdx.y * (G * EPL) + (int64_t)(lane % G) * EPL;
     int32_t *s_crd = reinterpret_cast<int32_t *>(batch_smem) + wid * 64;
     AT *s_val = reinterpret_cast<AT *>(batch_smem + wpb * 64 * sizeof(int32_t)) + wid * 64;
+    AT *s_cmp = reinterpret_cast<AT *>(batch_smem + wpb * 64 * sizeof(int32_t)) + wpb * 64 + wid * 32 * EPL;
     for (int64_t g = (int64_t)blockIdx.x * wpb + wid; g < total; g += nwarps) {
         const int64_t m = batch_of(pstart, count, g);
         const BatchDesc &d = descs[m];
@@ -65,11 +66,17 @@ __global__ void __launch_bounds__(256, kSpmmMinBlocks) spmm_batched_kernel(const
         const bool nnz_split = d.split == SPD_SPLIT_NNZ;
         const PieceBounds b = nnz_split ? nnz_piece(c, prow + d.part_off, ppos + d.part_off)
                                         : row_piece(c, d.P, d.n, d.pos);
-        spmm_piece<VT, EPL, U, FULLTILE>(d.n, d.pos, d.crd, static_cast<const VT *>(d.vals),
-                                         static_cast<const VT *>(d.X), d.ldx_bytes, static_cast<OT *>(d.Y), d.ldy, L,
-                                         b, col, lane, s_crd, s_val,
-                                         nnz_split ? carry_row + d.carry_off + c : nullptr, blockIdx.y == 0,
-                                         nnz_split ? carry_val + (d.carry_off + c) * L : nullptr);
+        const VT *vals = static_cast<const VT *>(d.vals);
+        const VT *X = static_cast<const VT *>(d.X);
+        OT *Y = static_cast<OT *>(d.Y);
+        int32_t *crow = nnz_split ? carry_row + d.carry_off + c : nullptr;
+        double *cval = nnz_split ? carry_val + (d.carry_off + c) * L : nullptr;
+        if constexpr (G == 32)
+            spmm_piece<VT, EPL, 4, FULLTILE>(d.n, d.pos, d.crd, vals, X, d.ldx_bytes, Y, d.ldy, L, b, col, lane, s_crd,
+                                             s_val, crow, blockIdx.y == 0, cval);
+        else
+            spmm_piece_grouped<VT, EPL, G, 4, FULLTILE>(d.n, d.pos, d.crd, vals, X, d.ldx_bytes, Y, d.ldy, L, b, col,
+                                                        lane, s_crd, s_val, s_cmp, crow, blockIdx.y == 0, cval);
     }
 }
 
@@ -157,9 +164,8 @@ static spd_status check_batch(int64_t count, const spd_batch_item *items, int64_
     return SPD_OK;
 }
 
-template <typename VT, int EPL, bool FULLTILE>
+template <typename VT, int EPL, int G, bool FULLTILE>
 static spd_status launch_batched(const spd_batch_plan *pl, cudaStream_t st) {
-    using AT = typename Traits<VT>::acc;
     using OT = typename Traits<VT>::out;
     char *w = static_cast<char *>(pl->ws);
     const BatchDesc *descs = reinterpret_cast<const BatchDesc *>(w + pl->off_desc);
@@ -168,10 +174,10 @@ static spd_status launch_batched(const spd_batch_plan *pl, cudaStream_t st) {
     const int32_t *ppos = reinterpret_cast<const int32_t *>(w + pl->off_ppos);
     int32_t *crow = reinterpret_cast<int32_t *>(w + pl->off_crow);
     double *cval = reinterpret_cast<double *>(w + pl->off_cval);
-    const int64_t ctiles = ceil_div(pl->L, 32 * EPL);
-    const size_t smem = (size_t)(pl->block_threads / 32) * 64 * (sizeof(int32_t) + sizeof(AT));
+    const int64_t ctiles = ceil_div(pl->L, G * EPL);
+    const size_t smem = (size_t)(pl->block_threads / 32) * spmm_warp_smem<VT>(EPL, G);
     dim3 grid((unsigned)pl->grid, (unsigned)ctiles);
-    spmm_batched_kernel<VT, EPL, 4, FULLTILE><<<grid, pl->block_threads, smem, st>>>(
+    spmm_batched_kernel<VT, EPL, G, FULLTILE><<<grid, pl->block_threads, smem, st>>>(
         descs, pstart, pl->count, pl->total_pieces, pl->L, prow, ppos, crow, cval);
     spd_status s = check_launch("spmm_batched_kernel");
     if (s || !pl->has_nnz) return s;
@@ -183,33 +189,21 @@ static spd_status launch_batched(const spd_batch_plan *pl, cudaStream_t st) {
 template <typename VT>
 static spd_status dispatch_batched(const spd_batch_plan *pl, cudaStream_t st) {
     const bool full = pl->fulltile != 0;
-    switch (pl->epl) {
-        case 1: return full ? launch_batched<VT, 1, true>(pl, st) : launch_batched<VT, 1, false>(pl, st);
-        case 2: return full ? launch_batched<VT, 2, true>(pl, st) : launch_batched<VT, 2, false>(pl, st);
-        case 4: return full ? launch_batched<VT, 4, true>(pl, st) : launch_batched<VT, 4, false>(pl, st);
-        default:
-            if constexpr (sizeof(VT) <= 4)
-                return full ? launch_batched<VT, 8, true>(pl, st) : launch_batched<VT, 8, false>(pl, st);
-            return full ? launch_batched<VT, 4, true>(pl, st) : launch_batched<VT, 4, false>(pl, st);
-    }
+    return with_lane_shape<VT>(pl->epl, pl->group, [&](auto sh) {
+        constexpr int E = decltype(sh)::epl, G = decltype(sh)::group;
+        return full ? launch_batched<VT, E, G, true>(pl, st) : launch_batched<VT, E, G, false>(pl, st);
+    });
 }
 
 template <typename VT>
-static int batched_blocks_per_sm(int epl, bool full, int threads) {
-    using AT = typename Traits<VT>::acc;
-    const size_t smem = (size_t)(threads / 32) * 64 * (sizeof(int32_t) + sizeof(AT));
+static int batched_blocks_per_sm(int epl, int group, bool full, int threads) {
+    const size_t smem = (size_t)(threads / 32) * spmm_warp_smem<VT>(epl, group);
     int blocks = 0;
-    cudaError_t e = cudaErrorInvalidValue;
-    switch (epl) {
-        case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, full ? spmm_batched_kernel<VT, 1, 4, true> : spmm_batched_kernel<VT, 1, 4, false>, threads, smem); break;
-        case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, full ? spmm_batched_kernel<VT, 2, 4, true> : spmm_batched_kernel<VT, 2, 4, false>, threads, smem); break;
-        case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, full ? spmm_batched_kernel<VT, 4, 4, true> : spmm_batched_kernel<VT, 4, 4, false>, threads, smem); break;
-        default:
-            if constexpr (sizeof(VT) <= 4)
-                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, full ? spmm_batched_kernel<VT, 8, 4, true> : spmm_batched_kernel<VT, 8, 4, false>, threads, smem);
-            else
-                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, full ? spmm_batched_kernel<VT, 4, 4, true> : spmm_batched_kernel<VT, 4, 4, false>, threads, smem);
-    }
+    const cudaError_t e = with_lane_shape<VT>(epl, group, [&](auto sh) {
+        constexpr int E = decltype(sh)::epl, G = decltype(sh)::group;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &blocks, full ? spmm_batched_kernel<VT, E, G, true> : spmm_batched_kernel<VT, E, G, false>, threads, smem);
+    });
     if (e != cudaSuccess || blocks < 1) {
         cudaGetLastError();
         return 1;
@@ -248,15 +242,30 @@ spd_status spd_spmm_batched_plan(int64_t count, const spd_batch_item *items, int
     if (!aligned(ws, 256)) return fail(SPD_ERR_ALIGN, "workspace not 256-byte aligned");
     cudaStream_t st = as_stream(stream);
 
-    // one element-per-lane width that suits every matrix
+    // one lane shape that suits every matrix: lane groups only when every matrix allows
+    // 16-byte vectors (decided by the largest X when the tuning leaves it open)
     const size_t vs = dtype_size(vtype), os = dtype_size(result_type(vtype));
-    int epl = 8;
+    uint64_t x_max = 0;
     for (int64_t m = 0; m < count; ++m) {
-        int e = pick_epl(L, vs, os, items[m].X, items[m].ldx, items[m].Y, items[m].ldy);
-        if (e < epl) epl = e;
+        const uint64_t xb = (uint64_t)items[m].A.ncols * (uint64_t)items[m].ldx * vs;
+        if (xb > x_max) x_max = xb;
     }
-    if (vs == 8 && epl > 4) epl = 4;
-    if (count == 0) epl = 1;
+    SpmmShape shape = pick_spmm_shape(L, vs, os, nullptr, 0, nullptr, 0, tn.lane_groups, x_max);
+    for (int64_t m = 0; m < count && shape.group < 32; ++m)
+        if (pick_spmm_shape(L, vs, os, items[m].X, items[m].ldx, items[m].Y, items[m].ldy, tn.lane_groups, x_max)
+                .group == 32)
+            shape.group = 32;
+    if (shape.group == 32) {  // 32 lanes at the narrowest width any matrix allows
+        int epl = 8;
+        for (int64_t m = 0; m < count; ++m) {
+            const int e = pick_epl(L, vs, os, items[m].X, items[m].ldx, items[m].Y, items[m].ldy);
+            if (e < epl) epl = e;
+        }
+        if (vs == 8 && epl > 4) epl = 4;
+        if (count == 0) epl = 1;
+        shape.epl = epl;
+    }
+    const int epl = shape.epl;
 
     std::vector<BatchDesc> descs((size_t)count);
     std::vector<int64_t> pstart((size_t)count + 1);
@@ -309,16 +318,16 @@ spd_status spd_spmm_batched_plan(int64_t count, const spd_batch_item *items, int
     e = cudaStreamSynchronize(st);  // the host copies of the descriptors end with this call
     if (e != cudaSuccess) return fail(SPD_ERR_CUDA, "plan: %s", cudaGetErrorString(e));
 
-    const bool full = L > 0 && L % (32 * epl) == 0;
+    const bool full = L > 0 && L % (shape.group * epl) == 0;
     int sms = 152;
     int dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int threads = tn.block_threads;
     int bps = 1;
     switch (vtype) {
-        case SPD_F64: bps = batched_blocks_per_sm<double>(epl, full, threads); break;
-        case SPD_F32: bps = batched_blocks_per_sm<float>(epl, full, threads); break;
-        default: bps = batched_blocks_per_sm<__nv_bfloat16>(epl, full, threads); break;
+        case SPD_F64: bps = batched_blocks_per_sm<double>(epl, shape.group, full, threads); break;
+        case SPD_F32: bps = batched_blocks_per_sm<float>(epl, shape.group, full, threads); break;
+        default: bps = batched_blocks_per_sm<__nv_bfloat16>(epl, shape.group, full, threads); break;
     }
     const int64_t need = ceil_div(piece > 0 ? piece : 1, threads / 32);
     int64_t grid = (int64_t)sms * bps;
@@ -329,6 +338,7 @@ spd_status spd_spmm_batched_plan(int64_t count, const spd_batch_item *items, int
     plan->L = L;
     plan->vtype = vtype;
     plan->epl = epl;
+    plan->group = shape.group;
     plan->block_threads = threads;
     plan->grid = (int32_t)grid;
     plan->fulltile = full ? 1 : 0;

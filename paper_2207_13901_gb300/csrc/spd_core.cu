@@ -65,6 +65,7 @@ spd_status read_tune(const spd_tune *t, Tuning *out) {
     out->row_pieces = 0;
     out->block_threads = kWarpBlockDefault;
     out->inflight = 8;
+    out->lane_groups = 0;
     if (!t) return SPD_OK;
     if (t->unit_items) {
         if (t->unit_items < 32 || t->unit_items > 65536 || t->unit_items % 32)
@@ -84,6 +85,8 @@ spd_status read_tune(const spd_tune *t, Tuning *out) {
         if (t->inflight != 4 && t->inflight != 8) return fail(SPD_ERR_ARG, "inflight %d is not 4 or 8", t->inflight);
         out->inflight = t->inflight;
     }
+    if (t->lane_groups < 0 || t->lane_groups > 2) return fail(SPD_ERR_ARG, "lane_groups %d not in 0..2", t->lane_groups);
+    out->lane_groups = t->lane_groups;
     return SPD_OK;
 }
 
@@ -146,6 +149,24 @@ int pick_epl(int64_t L, size_t in_size, size_t out_size, const void *in, int64_t
         epl /= 2;
     }
     return epl;
+}
+
+SpmmShape pick_spmm_shape(int64_t L, size_t in_size, size_t out_size, const void *in, int64_t ld_in,
+                          const void *out, int64_t ld_out, int lane_groups, uint64_t x_bytes) {
+    const int vec = (int)(16 / in_size);
+    const size_t vout = (size_t)vec * out_size;
+    const bool vec_ok = L > 0 && L % vec == 0 && ld_in % vec == 0 && ld_out % vec == 0 && aligned(in, 16) &&
+                        (out == nullptr || aligned(out, vout > 16 ? 16 : vout));
+    const bool want = lane_groups == 1 || (lane_groups == 0 && x_bytes <= (uint64_t(64) << 20));
+    if (vec_ok && want) {
+        const int64_t lanes = L / vec;
+        int g = 4;
+        while (g < lanes) g *= 2;
+        if (g < 32) return SpmmShape{vec, g};
+    }
+    int epl = pick_epl(L, in_size, out_size, in, ld_in, out, ld_out);
+    if (in_size == 8 && epl > 4) epl = 4;
+    return SpmmShape{epl, 32};
 }
 
 WsLayout layout_spmv(int64_t n, int64_t nnz, int split) {

@@ -292,6 +292,7 @@ struct Tuning {
     int64_t row_pieces;   // P of SPD_SPLIT_ROW (0 = per-kernel default)
     int block_threads;    // threads per block (warp kernels)
     int inflight;         // dense rows in flight per group (SpMM)
+    int lane_groups;      // SpMM lane shape: 0 = by the size of X, 1 = groups, 2 = 32 lanes
 };
 spd_status read_tune(const spd_tune *t, Tuning *out);
 int resolve_split(int split);
@@ -324,6 +325,17 @@ spd_status check_dense(const char *name, const void *p, int64_t rows, int64_t L,
 // dimensions allow vector accesses of that width.
 int pick_epl(int64_t L, size_t in_size, size_t out_size, const void *in, int64_t ld_in, const void *out,
              int64_t ld_out);
+
+// Lane shape of the SpMM kernels. group == 32: one entry per warp step, epl from
+// pick_epl. group in {4, 8, 16}: lane groups with one 16-byte vector per lane, used
+// when L needs fewer than 32 such lanes, the operands allow 16-byte vectors and
+// lane_groups asks for it (1) or leaves it to the size of X (0: x_bytes <= 64 MiB).
+struct SpmmShape {
+    int epl;
+    int group;
+};
+SpmmShape pick_spmm_shape(int64_t L, size_t in_size, size_t out_size, const void *in, int64_t ld_in,
+                          const void *out, int64_t ld_out, int lane_groups, uint64_t x_bytes);
 
 // Zero rows x L of a row-major matrix with leading dimension lda (one warp per row).
 template <typename OT>

@@ -15,7 +15,7 @@ namespace spd {
 
 constexpr unsigned FULL = kFullMask;
 
-template <typename VT, int EPL, int U, bool FULLTILE>
+template <typename VT, int EPL, int G, int U, bool FULLTILE>
 __global__ void __launch_bounds__(256, kSpmmMinBlocks) spmm_warp_kernel(
     int64_t n, const int32_t *__restrict__ pos, const int32_t *__restrict__ crd, const VT *__restrict__ vals,
     const VT *__restrict__ X, uint32_t ldx_bytes, typename Traits<VT>::out *__restrict__ Y, int64_t ldy, int64_t L,
@@ -25,15 +25,24 @@ __global__ void __launch_bounds__(256, kSpmmMinBlocks) spmm_warp_kernel(
     extern __shared__ __align__(16) unsigned char spmm_smem[];
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
-    const int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid;
+    const int wpb = blockDim.x >> 5;
+    const int64_t c = (int64_t)blockIdx.x * wpb + wid;
     if (c >= (prow ? npieces : P)) return;  // whole warp
-    const int64_t col = (int64_t)blockIdx.y * (32 * EPL) + (int64_t)lane * EPL;
     const PieceBounds b = prow ? nnz_piece(c, prow, ppos) : row_piece(c, P, n, pos);
     int32_t *s_crd = reinterpret_cast<int32_t *>(spmm_smem) + wid * 64;  // [2][32]
-    AT *s_val = reinterpret_cast<AT *>(spmm_smem + (blockDim.x >> 5) * 64 * sizeof(int32_t)) + wid * 64;
-    spmm_piece<VT, EPL, U, FULLTILE>(n, pos, crd, vals, X, ldx_bytes, Y, ldy, L, b, col, lane, s_crd, s_val,
-                                     carry_row ? carry_row + c : nullptr, blockIdx.y == 0,
-                                     carry_row ? carry_val + c * L : nullptr);
+    AT *s_val = reinterpret_cast<AT *>(spmm_smem + wpb * 64 * sizeof(int32_t)) + wid * 64;
+    int32_t *crow = carry_row ? carry_row + c : nullptr;
+    double *cval = carry_row ? carry_val + c * L : nullptr;
+    if constexpr (G == 32) {
+        const int64_t col = (int64_t)blockIdx.y * (32 * EPL) + (int64_t)lane * EPL;
+        spmm_piece<VT, EPL, U, FULLTILE>(n, pos, crd, vals, X, ldx_bytes, Y, ldy, L, b, col, lane, s_crd, s_val, crow,
+                                         blockIdx.y == 0, cval);
+    } else {
+        const int64_t col = (int64_t)blockIdx.y * (G * EPL) + (int64_t)(lane % G) * EPL;
+        AT *s_cmp = reinterpret_cast<AT *>(spmm_smem + wpb * 64 * sizeof(int32_t)) + wpb * 64 + wid * 32 * EPL;
+        spmm_piece_grouped<VT, EPL, G, U, FULLTILE>(n, pos, crd, vals, X, ldx_bytes, Y, ldy, L, b, col, lane, s_crd,
+                                                    s_val, s_cmp, crow, blockIdx.y == 0, cval);
+    }
 }
 
 // dX(j,l) = A(i,j) * dY(i,l): walk A's rows in the piece, keep the current row of dY in
@@ -104,21 +113,20 @@ static int64_t default_row_pieces(int64_t n, int64_t nnz, int64_t unit) {
     return P < 1 ? 1 : P;
 }
 
-template <typename VT, int EPL, int U, bool FULLTILE>
-static spd_status launch_spmm_epl(const spd_csr *A, const void *X, int64_t L, int64_t ldx, void *Y, int64_t ldy,
-                                  int split, const Tuning &tn, void *ws, cudaStream_t st) {
+template <typename VT, int EPL, int G, int U, bool FULLTILE>
+static spd_status launch_spmm_shape(const spd_csr *A, const void *X, int64_t L, int64_t ldx, void *Y, int64_t ldy,
+                                    int split, const Tuning &tn, void *ws, cudaStream_t st) {
     using OT = typename Traits<VT>::out;
-    using AT = typename Traits<VT>::acc;
     const int wpb = tn.block_threads / 32;
-    const int64_t ctiles = ceil_div(L, 32 * EPL);
-    const size_t smem = (size_t)wpb * 64 * (sizeof(int32_t) + sizeof(AT));  // two windows per warp
+    const int64_t ctiles = ceil_div(L, G * EPL);
+    const size_t smem = (size_t)wpb * spmm_warp_smem<VT>(EPL, G);
     const VT *v = static_cast<const VT *>(A->vals);
     const VT *x = static_cast<const VT *>(X);
     OT *y = static_cast<OT *>(Y);
     if (split == SPD_SPLIT_ROW) {
         const int64_t P = tn.row_pieces > 0 ? tn.row_pieces : default_row_pieces(A->nrows, A->nnz, tn.unit_items);
         dim3 grid((unsigned)ceil_div(P, wpb), (unsigned)ctiles);
-        spmm_warp_kernel<VT, EPL, U, FULLTILE><<<grid, tn.block_threads, smem, st>>>(
+        spmm_warp_kernel<VT, EPL, G, U, FULLTILE><<<grid, tn.block_threads, smem, st>>>(
             A->nrows, A->pos, A->crd, v, x, (uint32_t)(ldx * sizeof(VT)), y, ldy, L, nullptr, nullptr, 0, P, nullptr,
             nullptr);
         return check_launch("spmm_warp_kernel(row)");
@@ -132,44 +140,41 @@ static spd_status launch_spmm_epl(const spd_csr *A, const void *X, int64_t L, in
     spd_status s = launch_merge_partition(A->nrows, A->nnz, A->pos, tn.unit_items, Lw.npieces, prow, ppos, st);
     if (s) return s;
     dim3 grid((unsigned)ceil_div(Lw.npieces, wpb), (unsigned)ctiles);
-    spmm_warp_kernel<VT, EPL, U, FULLTILE><<<grid, tn.block_threads, smem, st>>>(
+    spmm_warp_kernel<VT, EPL, G, U, FULLTILE><<<grid, tn.block_threads, smem, st>>>(
         A->nrows, A->pos, A->crd, v, x, (uint32_t)(ldx * sizeof(VT)), y, ldy, L, prow, ppos, Lw.npieces, 0, crow,
         cval);
     if ((s = check_launch("spmm_warp_kernel(nnz)"))) return s;
     return launch_carry_fixup<OT>(Lw.npieces, L, crow, cval, y, ldy, st);
 }
 
-template <typename VT, int EPL, bool FULLTILE>
-static spd_status launch_spmm_f(const spd_csr *A, const void *X, int64_t L, int64_t ldx, void *Y, int64_t ldy,
-                                int split, const Tuning &tn, void *ws, cudaStream_t st) {
-    if constexpr (sizeof(VT) == 8) {
-        return launch_spmm_epl<VT, EPL, 4, FULLTILE>(A, X, L, ldx, Y, ldy, split, tn, ws, st);
-    } else {
-        if (tn.inflight == 4) return launch_spmm_epl<VT, EPL, 4, FULLTILE>(A, X, L, ldx, Y, ldy, split, tn, ws, st);
-        return launch_spmm_epl<VT, EPL, 8, FULLTILE>(A, X, L, ldx, Y, ldy, split, tn, ws, st);
-    }
-}
-
-template <typename VT, int EPL>
+// Rows in flight per group: the tuning's 4 or 8 for one entry per warp step in the
+// binary32 modes; 4 for binary64 (8 would spill) and for lane groups.
+template <typename VT, int EPL, int G>
 static spd_status launch_spmm_u(const spd_csr *A, const void *X, int64_t L, int64_t ldx, void *Y, int64_t ldy,
                                 int split, const Tuning &tn, void *ws, cudaStream_t st) {
-    if (L % (32 * EPL) == 0) return launch_spmm_f<VT, EPL, true>(A, X, L, ldx, Y, ldy, split, tn, ws, st);
-    return launch_spmm_f<VT, EPL, false>(A, X, L, ldx, Y, ldy, split, tn, ws, st);
+    const bool full = L % (G * EPL) == 0;
+    if constexpr (sizeof(VT) == 8 || G < 32) {
+        return full ? launch_spmm_shape<VT, EPL, G, 4, true>(A, X, L, ldx, Y, ldy, split, tn, ws, st)
+                    : launch_spmm_shape<VT, EPL, G, 4, false>(A, X, L, ldx, Y, ldy, split, tn, ws, st);
+    } else {
+        if (tn.inflight == 4)
+            return full ? launch_spmm_shape<VT, EPL, G, 4, true>(A, X, L, ldx, Y, ldy, split, tn, ws, st)
+                        : launch_spmm_shape<VT, EPL, G, 4, false>(A, X, L, ldx, Y, ldy, split, tn, ws, st);
+        return full ? launch_spmm_shape<VT, EPL, G, 8, true>(A, X, L, ldx, Y, ldy, split, tn, ws, st)
+                    : launch_spmm_shape<VT, EPL, G, 8, false>(A, X, L, ldx, Y, ldy, split, tn, ws, st);
+    }
 }
 
 template <typename VT>
 static spd_status launch_spmm(const spd_csr *A, const void *X, int64_t L, int64_t ldx, void *Y, int64_t ldy,
                               int split, const Tuning &tn, void *ws, cudaStream_t st) {
     using OT = typename Traits<VT>::out;
-    int epl = pick_epl(L, sizeof(VT), sizeof(OT), X, ldx, Y, ldy);
-    switch (epl) {
-        case 1: return launch_spmm_u<VT, 1>(A, X, L, ldx, Y, ldy, split, tn, ws, st);
-        case 2: return launch_spmm_u<VT, 2>(A, X, L, ldx, Y, ldy, split, tn, ws, st);
-        case 4: return launch_spmm_u<VT, 4>(A, X, L, ldx, Y, ldy, split, tn, ws, st);
-        default:
-            if constexpr (sizeof(VT) <= 4) return launch_spmm_u<VT, 8>(A, X, L, ldx, Y, ldy, split, tn, ws, st);
-            return launch_spmm_u<VT, 4>(A, X, L, ldx, Y, ldy, split, tn, ws, st);
-    }
+    const SpmmShape sh = pick_spmm_shape(L, sizeof(VT), sizeof(OT), X, ldx, Y, ldy, tn.lane_groups,
+                                         (uint64_t)A->ncols * (uint64_t)ldx * sizeof(VT));
+    return with_lane_shape<VT>(sh.epl, sh.group, [&](auto shape) {
+        constexpr int E = decltype(shape)::epl, G = decltype(shape)::group;
+        return launch_spmm_u<VT, E, G>(A, X, L, ldx, Y, ldy, split, tn, ws, st);
+    });
 }
 
 template <typename VT, int EPL>

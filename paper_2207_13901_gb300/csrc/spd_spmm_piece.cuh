@@ -182,4 +182,261 @@ __device__ __forceinline__ void spmm_piece(int64_t n, const int32_t *__restrict_
     }
 }
 
+// One lane's EPL elements of a row of X, as loaded by one vector access. bfloat16
+// elements stay packed two per register and are widened only when multiplied (exactly:
+// a bfloat16 is the upper half of the binary32 of the same value).
+template <typename VT, int EPL>
+struct XVec {
+    VT v[EPL];
+    __device__ __forceinline__ void load(const VT *p) { ld_vec<EPL>(p, v); }
+    __device__ __forceinline__ void clear() { zero(v); }
+    __device__ __forceinline__ VT at(int e) const { return v[e]; }
+};
+template <int EPL>
+struct XVec<__nv_bfloat16, EPL> {
+    static constexpr int W = EPL >= 2 ? EPL / 2 : 1;
+    uint32_t w[W];
+    __device__ __forceinline__ void load(const __nv_bfloat16 *p) {
+        if constexpr (EPL == 1) {
+            w[0] = (uint32_t)__bfloat16_as_ushort(__ldg(p));
+        } else if constexpr (EPL == 2) {
+            w[0] = __ldg(reinterpret_cast<const unsigned int *>(p));
+        } else if constexpr (EPL == 4) {
+            const uint2 r = __ldg(reinterpret_cast<const uint2 *>(p));
+            w[0] = r.x; w[1] = r.y;
+        } else {
+#pragma unroll
+            for (int q = 0; q < EPL / 8; ++q) {
+                const uint4 r = __ldg(reinterpret_cast<const uint4 *>(p) + q);
+                w[4 * q] = r.x; w[4 * q + 1] = r.y; w[4 * q + 2] = r.z; w[4 * q + 3] = r.w;
+            }
+        }
+    }
+    __device__ __forceinline__ void clear() { zero(w); }
+    __device__ __forceinline__ float at(int e) const {
+        const uint32_t x = w[e >> 1];
+        return __uint_as_float((e & 1) ? (x & 0xffff0000u) : (x << 16));
+    }
+};
+
+// The same piece computed by lane groups: NG = 32/G groups of G lanes, each lane with
+// one 16-byte vector (EPL elements) of the G*EPL columns starting at `col` (this lane's
+// first column). For narrow L (G*EPL < 32*EPL of spmm_piece) the groups take different
+// entries of the same rows side by side, so every gather instruction still moves a full
+// vector per lane. Each group keeps its own partial of the current row; the partials
+// are summed across the groups (a butterfly over the lane bits above G) when the row is
+// written or carried, and group 0 writes. Entry q of a 32-entry window sits in slot
+// (q % NG) * G + q / NG so that the U entries a group takes in one step are adjacent.
+// s_cmp: this warp's 32*EPL slots for the Kahan compensations of a long row (kept out of
+// registers, long rows being rare). Other arguments as for spmm_piece.
+template <typename VT, int EPL, int G, int U, bool FULLTILE>
+__device__ __forceinline__ void spmm_piece_grouped(int64_t n, const int32_t *__restrict__ pos,
+                                                   const int32_t *__restrict__ crd, const VT *__restrict__ vals,
+                                                   const VT *__restrict__ X, uint32_t ldx_bytes,
+                                                   typename Traits<VT>::out *__restrict__ Y, int64_t ldy, int64_t L,
+                                                   const PieceBounds b, const int64_t col, const int lane,
+                                                   int32_t *s_crd, typename Traits<VT>::acc *s_val,
+                                                   typename Traits<VT>::acc *s_cmp, int32_t *carry_row,
+                                                   bool write_carry_row, double *carry_val) {
+    using AT = typename Traits<VT>::acc;
+    using OT = typename Traits<VT>::out;
+    constexpr int NG = 32 / G;    // entries consumed side by side
+    constexpr int STEP = NG * U;  // entries per step of the warp
+    static_assert(G >= 4 && G < 32 && (G & (G - 1)) == 0, "group width");
+    static_assert(U % 4 == 0 && U <= G, "a step must fit in one window");
+    const int gi = lane / G;
+    const bool active = FULLTILE || col < L;
+    const bool writer = active && gi == 0;
+    const int my_slot = (lane % NG) * G + lane / NG;
+    const char *__restrict__ Xc = reinterpret_cast<const char *>(X + col);
+    auto xrow = [&](int32_t j) { return reinterpret_cast<const VT *>(Xc + (uint64_t)(uint32_t)j * ldx_bytes); };
+
+    AT acc[EPL];
+    zero(acc);
+    AT *cmp = s_cmp + lane;  // compensation of element e at cmp[32 * e]
+    bool touched = false;    // some group accumulated an entry of row r (warp-uniform)
+    int32_t r = b.r0;
+    RowWindow win;
+    win.load(r, n, pos, lane);
+    int32_t cur_start = r < n ? __ldg(pos + r) : b.p1;
+    int32_t true_end = r < n ? win.end_of(r) : INT_MAX;
+    int32_t cur_end = r < b.r1 ? true_end : INT_MAX;
+    bool kahan = (sizeof(AT) == 4) && (true_end - cur_start > kLongRow);
+    auto clear_cmp = [&]() {
+#pragma unroll
+        for (int e = 0; e < EPL; ++e) cmp[32 * e] = (AT)0;
+    };
+    if (kahan) clear_cmp();
+
+    auto emit = [&]() {
+        if (kahan) {
+#pragma unroll
+            for (int e = 0; e < EPL; ++e) acc[e] -= cmp[32 * e];
+        }
+        if (touched) {
+#pragma unroll
+            for (int e = 0; e < EPL; ++e) {
+#pragma unroll
+                for (int m = G; m < 32; m <<= 1) acc[e] += __shfl_xor_sync(kFullMask, acc[e], m);
+            }
+        }
+        if (writer) {
+            OT o[EPL];
+#pragma unroll
+            for (int e = 0; e < EPL; ++e) o[e] = (OT)acc[e];
+            st_vec(Y + (int64_t)r * ldy + col, o);
+        }
+        zero(acc);
+        touched = false;
+        cur_start = cur_end;
+        ++r;
+        if (r - win.rw == 32) win.load(r, n, pos, lane);
+        true_end = r < n ? win.end_of(r) : INT_MAX;
+        cur_end = r < b.r1 ? true_end : INT_MAX;
+        kahan = (sizeof(AT) == 4) && (true_end - cur_start > kLongRow);
+        if (kahan) clear_cmp();
+    };
+
+    int32_t pb = b.p0;
+    int cnt = (b.p1 - pb) < 32 ? (b.p1 - pb) : 32;
+    int buf = 0;
+    s_crd[my_slot] = lane < cnt ? ld_stream(crd + pb + lane) : 0;
+    s_val[my_slot] = lane < cnt ? (AT)ld_stream(vals + pb + lane) : (AT)0;
+    __syncwarp();
+    while (pb < b.p1) {
+        const int32_t pn = pb + 32;
+        const int cnt_n = b.p1 - pn <= 0 ? 0 : (b.p1 - pn < 32 ? b.p1 - pn : 32);
+        const int32_t c_n = lane < cnt_n ? ld_stream(crd + pn + lane) : 0;
+        const AT v_n = lane < cnt_n ? (AT)ld_stream(vals + pn + lane) : (AT)0;
+        const int32_t *wc = s_crd + buf * 32;
+        const AT *wv = s_val + buf * 32;
+#pragma unroll 1
+        for (int j0 = 0; j0 < cnt; j0 += STEP) {
+            XVec<VT, EPL> xv[U];
+            int32_t cj[U];
+            AT vj[U];
+            const int sb = gi * G + j0 / NG;  // slot of this group's first entry of the step
+#pragma unroll
+            for (int q = 0; q < U / 4; ++q) {
+                const int4 c4 = *reinterpret_cast<const int4 *>(wc + sb + 4 * q);
+                cj[4 * q] = c4.x; cj[4 * q + 1] = c4.y; cj[4 * q + 2] = c4.z; cj[4 * q + 3] = c4.w;
+            }
+            const int gcnt = cnt - j0 < STEP ? cnt - j0 : STEP;  // valid entries of this step
+            if (active && gcnt == STEP) {
+#pragma unroll
+                for (int u = 0; u < U; ++u) xv[u].load(xrow(cj[u]));
+            } else {
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    if (active && u * NG + gi < gcnt) xv[u].load(xrow(cj[u]));
+                    else xv[u].clear();
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) vj[u] = wv[sb + u];
+            if (!kahan && gcnt == STEP && (int64_t)pb + j0 + STEP <= (int64_t)cur_end) {
+                // fast path: the whole step lies inside the current row
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+#pragma unroll
+                    for (int e = 0; e < EPL; ++e) acc[e] = fma(vj[u], (AT)xv[u].at(e), acc[e]);
+                }
+                touched = true;
+                continue;
+            }
+            // general path: one row segment at a time (entry k of the step is u*NG + gi)
+            int lo = 0;
+            while (lo < gcnt) {
+                while (cur_end <= pb + j0 + lo) emit();
+                const int64_t in_row = (int64_t)cur_end - (pb + j0);
+                const int hi = in_row < gcnt ? (int)in_row : gcnt;
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int k = u * NG + gi;
+                    if (k >= lo && k < hi) {
+                        if (kahan) {
+#pragma unroll
+                            for (int e = 0; e < EPL; ++e) {
+                                AT c = cmp[32 * e];
+                                kahan_fma(acc[e], c, vj[u], (AT)xv[u].at(e));
+                                cmp[32 * e] = c;
+                            }
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < EPL; ++e) acc[e] = fma(vj[u], (AT)xv[u].at(e), acc[e]);
+                        }
+                    }
+                }
+                touched = true;
+                lo = hi;
+            }
+        }
+        buf ^= 1;
+        __syncwarp();
+        s_crd[buf * 32 + my_slot] = c_n;
+        s_val[buf * 32 + my_slot] = v_n;
+        __syncwarp();
+        pb = pn;
+        cnt = cnt_n;
+    }
+    while (r < b.r1) emit();
+
+    if (carry_row) {
+        int32_t start = b.r1 < n ? __ldg(pos + b.r1) : b.p1;
+        if (start < b.p0) start = b.p0;
+        const bool has = b.p1 > start;  // warp-uniform
+        if (lane == 0 && write_carry_row) *carry_row = has ? b.r1 : -1;
+        if (has) {
+            double t[EPL];
+#pragma unroll
+            for (int e = 0; e < EPL; ++e) {
+                t[e] = (double)acc[e] - (kahan ? (double)cmp[32 * e] : 0.0);
+#pragma unroll
+                for (int m = G; m < 32; m <<= 1) t[e] += __shfl_xor_sync(kFullMask, t[e], m);
+            }
+            if (writer) {
+#pragma unroll
+                for (int e = 0; e < EPL; ++e) carry_val[col + e] = t[e];
+            }
+        }
+    }
+}
+
+// Lane shape of the SpMM kernels: EPL elements per lane and groups of G lanes. G == 32
+// runs spmm_piece (one entry per warp step), G < 32 spmm_piece_grouped with 16-byte
+// vectors.
+template <int E, int G_>
+struct LaneShape {
+    static constexpr int epl = E;
+    static constexpr int group = G_;
+};
+
+// Shared memory of one warp of an SpMM kernel: two crd/vals windows, plus the Kahan
+// slots of the grouped body.
+template <typename VT>
+inline size_t spmm_warp_smem(int epl, int group) {
+    using AT = typename Traits<VT>::acc;
+    return 64 * (sizeof(int32_t) + sizeof(AT)) + (group < 32 ? (size_t)32 * epl * sizeof(AT) : 0);
+}
+
+// Calls f(LaneShape<EPL, G>{}) for a lane shape chosen by pick_spmm_shape: grouped
+// shapes use the 16-byte vector of VT; G == 32 shapes any EPL in 1..8 (1..4 binary64).
+template <typename VT, typename F>
+inline auto with_lane_shape(int epl, int group, F &&f) {
+    constexpr int V = (int)(16 / sizeof(VT));
+    if (group < 32) {
+        if (group == 4) return f(LaneShape<V, 4>{});
+        if (group == 8) return f(LaneShape<V, 8>{});
+        return f(LaneShape<V, 16>{});
+    }
+    switch (epl) {
+        case 1: return f(LaneShape<1, 32>{});
+        case 2: return f(LaneShape<2, 32>{});
+        case 4: return f(LaneShape<4, 32>{});
+        default:
+            if constexpr (sizeof(VT) <= 4) return f(LaneShape<8, 32>{});
+            return f(LaneShape<4, 32>{});
+    }
+}
+
 }  // namespace spd
