@@ -62,6 +62,8 @@ _SIGS = {
     "orc_spmttkrp_acc": [_I64, _I64, _P, _P, _P, _P, _P, _P, _I64, _P, _I64, _I64, _P, _P, _I64],
     "orc_validate_level": [_I64, _I64, _P, _P, _I64, _P],
     "orc_csr_transpose": [_I64, _I64, _P, _P, _P, _P, _P],
+    "orc_spadd3_count": [_I64, _P, _P, _P, _P, _P, _P, _P],
+    "orc_spadd3": [_I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P],
 }
 
 
@@ -140,6 +142,28 @@ def csr_transpose(pos, crd, ncols: int):
     perm = np.zeros(nnz, dtype=np.int32)
     lib().orc_csr_transpose(pos.shape[0] - 1, ncols, _ptr(pos), _ptr(crd), _ptr(t_pos), _ptr(t_crd), _ptr(perm))
     return t_pos, t_crd, perm
+
+
+def spadd3_count(B, C, D) -> np.ndarray:
+    """Entries per row of A = B + C + D (the union of the three patterns)."""
+    ops = [(_i32(M.pos), _i32(M.crd)) for M in (B, C, D)]
+    n = ops[0][0].shape[0] - 1
+    out = np.zeros(n, dtype=np.int64)
+    lib().orc_spadd3_count(n, *[_ptr(a) for pc in ops for a in pc], _ptr(out))
+    return out
+
+
+def spadd3(B, C, D):
+    """(pos, crd, vals) of A = B + C + D; B, C, D are objects with pos/crd/vals (one shape)."""
+    ops = [(_i32(M.pos), _i32(M.crd), _f64(M.vals)) for M in (B, C, D)]
+    n = ops[0][0].shape[0] - 1
+    total = int(sum(M.crd.shape[0] for M in (B, C, D)))
+    ap = np.zeros(n + 1, dtype=np.int32)
+    ac = np.zeros(max(total, 1), dtype=np.int32)
+    av = np.zeros(max(total, 1), dtype=np.float64)
+    lib().orc_spadd3(n, *[_ptr(a) for t in ops for a in t], _ptr(ap), _ptr(ac), _ptr(av))
+    nnz = int(ap[-1])
+    return ap, ac[:nnz].copy(), av[:nnz].copy()
 
 
 def validate_level(nparent: int, nchild_dim: int, pos, crd):

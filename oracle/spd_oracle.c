@@ -433,3 +433,52 @@ void orc_csr_transpose(int64_t n, int64_t ncols, const int32_t *pos, const int32
         }
     free(next);
 }
+
+/* ------------------------------------------------------------------------------------
+ * SpAdd3 A(i,j) = B(i,j) + C(i,j) + D(i,j) (Section VI-A) on CSR operands of one shape.
+ * A's structure is not known in advance: it is the union of the three patterns
+ * (every coordinate stored in any input is stored in A, even where the values cancel).
+ * Assembly in two phases as in Section V-B: orc_spadd3_count writes the number of
+ * entries of each row of A (row i's union size), and orc_spadd3 fills A's pos, crd and
+ * vals. Rows are merged in ascending column order; a value is formed left to right as
+ * the statement is written, (B + C) + D, over the operands that store the coordinate.
+ * Each input row must hold ascending, distinct columns.
+ * ------------------------------------------------------------------------------------ */
+static int64_t spadd3_row(int64_t i, const int32_t *bp, const int32_t *bc, const double *bv,
+                          const int32_t *cp, const int32_t *cc, const double *cv,
+                          const int32_t *dp, const int32_t *dc, const double *dv,
+                          int32_t *out_crd, double *out_val) {
+    int64_t pb = bp[i], pc = cp[i], pd = dp[i], k = 0;
+    const int64_t eb = bp[i + 1], ec = cp[i + 1], ed = dp[i + 1];
+    while (pb < eb || pc < ec || pd < ed) {
+        int64_t j = INT64_MAX;  /* smallest column still to merge */
+        if (pb < eb && bc[pb] < j) j = bc[pb];
+        if (pc < ec && cc[pc] < j) j = cc[pc];
+        if (pd < ed && dc[pd] < j) j = dc[pd];
+        double v = 0.0;
+        int have = 0;
+        if (pb < eb && bc[pb] == j) { v = bv ? bv[pb] : 0.0; have = 1; ++pb; }
+        if (pc < ec && cc[pc] == j) { double t = cv ? cv[pc] : 0.0; v = have ? v + t : t; have = 1; ++pc; }
+        if (pd < ed && dc[pd] == j) { double t = dv ? dv[pd] : 0.0; v = have ? v + t : t; ++pd; }
+        if (out_crd) { out_crd[k] = (int32_t)j; out_val[k] = v; }
+        ++k;
+    }
+    return k;
+}
+
+void orc_spadd3_count(int64_t n, const int32_t *bp, const int32_t *bc, const int32_t *cp,
+                      const int32_t *cc, const int32_t *dp, const int32_t *dc, int64_t *row_nnz) {
+    for (int64_t i = 0; i < n; ++i)
+        row_nnz[i] = spadd3_row(i, bp, bc, NULL, cp, cc, NULL, dp, dc, NULL, NULL, NULL);
+}
+
+void orc_spadd3(int64_t n, const int32_t *bp, const int32_t *bc, const double *bv,
+                const int32_t *cp, const int32_t *cc, const double *cv,
+                const int32_t *dp, const int32_t *dc, const double *dv,
+                int32_t *ap, int32_t *ac, double *av) {
+    ap[0] = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t k = spadd3_row(i, bp, bc, bv, cp, cc, cv, dp, dc, dv, ac + ap[i], av + ap[i]);
+        ap[i + 1] = (int32_t)(ap[i] + k);
+    }
+}

@@ -250,6 +250,56 @@ def uniform_csr(nrows: int, ncols: int, nnz_per_row, seed: int = 0,
     return CSR(nrows, ncols, starts.astype(np.int32), cols.astype(np.int32), vals)
 
 
+def banded_csr(nrows: int, half_width: int, seed: int = 0, value_dtype=np.float64) -> CSR:
+    """Square banded matrix: row i holds every column in [i - w, i + w] inside [0, n)
+    (2w + 1 per interior row), values uniform in [-1, 1) from the stream ``seed`` drawn
+    in position order (on the binary32 grid when ``value_dtype`` is float32). The
+    structure is written directly, row block by row block, with no sorting."""
+    n, w = int(nrows), int(half_width)
+    i = np.arange(n, dtype=np.int64)
+    lo = np.maximum(i - w, 0)
+    hi = np.minimum(i + w, n - 1)
+    pos = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(hi - lo + 1, out=pos[1:])
+    nnz = int(pos[-1])
+    crd = np.empty(nnz, dtype=np.int32)
+    step = 1 << 20
+    for r0 in range(0, n, step):
+        r1 = min(n, r0 + step)
+        p0, p1 = int(pos[r0]), int(pos[r1])
+        # column of position p in row r = lo[r] + (p - pos[r])
+        off = np.repeat((lo[r0:r1] - pos[r0:r1]).astype(np.int64), (hi[r0:r1] - lo[r0:r1] + 1))
+        crd[p0:p1] = (off + np.arange(p0, p1, dtype=np.int64)).astype(np.int32)
+    vals = uniform(nnz, seed, dtype=value_dtype).astype(np.float64) if value_dtype == np.float64 else \
+        uniform(nnz, seed, dtype=np.float32)
+    return CSR(n, n, pos.astype(np.int32), crd, vals)
+
+
+def shifted_csr(A: CSR, shift: int, seed: int, value_dtype=np.float64) -> CSR:
+    """A's pattern with every column moved by ``shift`` (mod ncols) -- the way the paper
+    builds the extra operands of a multi-input statement from one matrix -- and fresh
+    values uniform in [-1, 1) from the stream ``seed``. Rows stay sorted: the entries
+    that wrap around (a suffix of each sorted row) move to the front."""
+    n, m = A.nrows, A.ncols
+    crd = A.crd.astype(np.int64)
+    lens = np.diff(A.pos).astype(np.int64)
+    starts = np.repeat(A.pos[:-1].astype(np.int64), lens)
+    off = np.arange(crd.shape[0], dtype=np.int64) - starts  # offset inside the row
+    newc = crd + shift
+    wrapped = newc >= m
+    cw = np.concatenate([[0], np.cumsum(wrapped, dtype=np.int64)])
+    w = cw[A.pos[1:]] - cw[A.pos[:-1]]  # wrapped entries per row
+    w_e = np.repeat(w, lens)
+    len_e = np.repeat(lens, lens)
+    dest = starts + np.where(wrapped, off - (len_e - w_e), off + w_e)
+    out = np.empty(crd.shape[0], dtype=np.int32)
+    out[dest] = (newc % m).astype(np.int32) if m else newc.astype(np.int32)
+    vals = uniform(crd.shape[0], seed, dtype=value_dtype)
+    if value_dtype != np.float32:
+        vals = vals.astype(np.float64)
+    return CSR(n, m, A.pos.copy(), out, vals)
+
+
 def batched_uniform_csr(count: int, rows_lo: float, rows_hi: float, nnz_lo: int, nnz_hi: int,
                         seed: int = 0) -> List[CSR]:
     """``count`` square CSR matrices: rows log-uniform in [rows_lo, rows_hi],

@@ -94,6 +94,16 @@ def test_golden_transpose():
     assert np.array_equal(g["vals"][perm], g["t_vals"])
 
 
+def test_golden_spadd3():
+    g = read_golden("spadd3_3x4.txt")
+    n, m = int(g["nrows"][0]), int(g["ncols"][0])
+    B, C, D = [spd_synth.CSR(n, m, g[k + "_pos"], g[k + "_crd"], g[k + "_vals"].astype(np.float64)) for k in "bcd"]
+    assert np.array_equal(oracle.spadd3_count(B, C, D), g["row_nnz"])
+    ap, ac, av = oracle.spadd3(B, C, D)
+    assert np.array_equal(ap, g["a_pos"]) and np.array_equal(ac, g["a_crd"])
+    assert np.array_equal(av, g["a_vals"])
+
+
 # ------------------------------------------------------------------------------ dense brute force
 
 @pytest.mark.parametrize("seed", SEEDS)
@@ -419,6 +429,56 @@ def test_transpose_against_scipy_csc():
     t_pos, t_crd, perm = oracle.csr_transpose(A.pos, A.crd, A.ncols)
     assert np.array_equal(t_pos, S.indptr) and np.array_equal(t_crd, S.indices)
     assert np.array_equal(A.vals[perm], S.data)
+
+
+# ------------------------------------------------------------------------------ SpAdd3
+
+def _spadd3_operands(rng, n, m, density, integer):
+    return [small_csr(rng, n, m, density, long_rows=1, integer=integer) for _ in range(3)]
+
+
+@pytest.mark.parametrize("seed", SEEDS)
+def test_spadd3_dense_bruteforce_and_union(seed):
+    """Values equal the dense sum exactly (small integers); the pattern is the union of
+    the three patterns, kept even where values cancel; counts agree with pos."""
+    rng = np.random.default_rng(seed)
+    B, C, D = _spadd3_operands(rng, 29, 17, 0.2, integer=True)
+    C.vals[: C.nnz // 2] = 0.0  # stored zeros stay stored
+    ap, ac, av = oracle.spadd3(B, C, D)
+    A = spd_synth.CSR(29, 17, ap, ac, av)
+    assert np.array_equal(dense_of_csr(A), dense_of_csr(B) + dense_of_csr(C) + dense_of_csr(D))
+    for i in range(29):
+        want = set(B.crd[B.pos[i]:B.pos[i + 1]]) | set(C.crd[C.pos[i]:C.pos[i + 1]]) | set(D.crd[D.pos[i]:D.pos[i + 1]])
+        row = ac[ap[i]:ap[i + 1]]
+        assert list(row) == sorted(want)
+    assert np.array_equal(oracle.spadd3_count(B, C, D), np.diff(ap))
+
+
+def test_spadd3_special_cases():
+    rng = np.random.default_rng(7)
+    B = small_csr(rng, 40, 30, 0.2, long_rows=1)
+    E = spd_synth.csr_from_coords(40, 30, [], [], vals=np.zeros(0))
+    ap, ac, av = oracle.spadd3(B, E, E)  # adding empty matrices gives B back
+    assert np.array_equal(ap, B.pos) and np.array_equal(ac, B.crd) and np.array_equal(av, B.vals)
+    ap, ac, av = oracle.spadd3(E, E, B)
+    assert np.array_equal(ac, B.crd) and np.array_equal(av, B.vals)
+    ap, ac, av = oracle.spadd3(B, B, B)  # same pattern three times: (b + b) + b
+    assert np.array_equal(ap, B.pos) and np.array_equal(ac, B.crd) and np.array_equal(av, (B.vals + B.vals) + B.vals)
+
+
+def test_spadd3_against_scipy():
+    sp = pytest.importorskip("scipy.sparse")
+    A = spd_synth.rmat_csr(10, 8, seed=8)
+    ops = [spd_synth.CSR(A.nrows, A.ncols, A.pos, A.crd, np.abs(A.vals) + 0.5)]
+    ops += [spd_synth.shifted_csr(A, s, seed=9 + s) for s in (1, 2)]
+    ops[1].vals = np.abs(ops[1].vals) + 0.5  # positive: scipy prunes exact zeros, the oracle keeps them
+    ops[2].vals = np.abs(ops[2].vals) + 0.5
+    S = [sp.csr_matrix((M.vals, M.crd, M.pos), shape=(A.nrows, A.ncols)) for M in ops]
+    R = ((S[0] + S[1]) + S[2]).tocsr()
+    R.sort_indices()
+    ap, ac, av = oracle.spadd3(*ops)
+    assert np.array_equal(ap, R.indptr) and np.array_equal(ac, R.indices)
+    assert np.array_equal(av, R.data)
 
 
 # ------------------------------------------------------------------------------ library cross-check

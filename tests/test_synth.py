@@ -46,3 +46,28 @@ def test_rmat_and_zipf_invariants():
     assert oracle.validate_level(T.dims[0], T.dims[1], T.pos1, T.crd1) == (0, -1)
     assert oracle.validate_level(T.nfib, T.dims[2], T.pos2, T.crd2) == (0, -1)
     assert np.all(np.diff(T.pos2) > 0)  # no empty fibers
+
+
+def test_banded_structure():
+    """Row i holds exactly the columns max(0, i-w) .. min(n-1, i+w), in order."""
+    n, w = 50, 3
+    A = spd_synth.banded_csr(n, w, seed=1)
+    dense = np.zeros((n, n), dtype=bool)
+    for i in range(n):
+        cols = A.crd[A.pos[i]:A.pos[i + 1]]
+        assert np.all(np.diff(cols) == 1)
+        dense[i, cols] = True
+    ii, jj = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    assert np.array_equal(dense, np.abs(ii - jj) <= w)
+    assert A.nnz == n * (2 * w + 1) - w * (w + 1)
+    assert np.all((A.vals >= -1) & (A.vals < 1))
+
+
+def test_shifted_csr_rotates_each_row():
+    A = spd_synth.rmat_csr(9, 8, seed=2)
+    for shift in (1, 2, A.ncols - 1):
+        S = spd_synth.shifted_csr(A, shift, seed=3)
+        assert np.array_equal(S.pos, A.pos)
+        for i in range(A.nrows):
+            got = S.crd[S.pos[i]:S.pos[i + 1]]
+            assert np.array_equal(got, np.sort((A.crd[A.pos[i]:A.pos[i + 1]] + shift) % A.ncols))
