@@ -55,7 +55,8 @@ def parse_args(argv=None):
     p.add_argument("--fixed-tune", default="",
                    help="UNIT,BLOCK,INFLIGHT: skip the autotuner and run SpMM with this tuning (nnz split)")
     p.add_argument("--rows", default="all",
-                   help="comma list of extra hot-path rows to measure: cfg1,sddmm,backward,csf,batched (or all, none)")
+                   help="comma list of extra hot-path rows to measure: cfg1,sddmm,backward,csf,batched,banded,spadd3 "
+                        "(or all, none)")
     return p.parse_args(argv)
 
 
@@ -442,11 +443,12 @@ def run_gpu(args):
         cpu = cpu_baseline(A, x32, X32, args.cpu_budget)
 
     rows_out = {}
-    wanted = {"cfg1", "sddmm", "backward", "csf", "batched"} if args.rows == "all" else \
+    wanted = {"cfg1", "sddmm", "backward", "csf", "batched", "banded", "spadd3"} if args.rows == "all" else \
         (set() if args.rows == "none" else set(args.rows.split(",")))
     for name, fn in (("cfg1", lambda: row_cfg1(hbm)), ("backward", lambda: row_backward(A, X32, hbm)),
                      ("sddmm", lambda: row_sddmm(hbm)), ("csf", lambda: row_csf(hbm)),
-                     ("batched", lambda: row_batched(hbm))):
+                     ("batched", lambda: row_batched(hbm)), ("banded", lambda: row_banded(hbm)),
+                     ("spadd3", lambda: row_spadd3(A, hbm))):
         if name not in wanted:
             continue
         if name == "backward":
@@ -580,6 +582,84 @@ def row_cfg1(hbm):
         oracle.spmv(A.pos, A.crd, A.vals, x)
     dt = (time.perf_counter() - t) / 20
     out["oracle"] = {"nnz_per_s": A.nnz / dt, "cores": 1, "sample": "whole matrix"}
+    return out
+
+
+def row_spadd3(A, hbm):
+    """SpAdd3 A = B + C + D on the 2^22 R-MAT: B is the matrix, C and D its columns
+    shifted by 1 and 2 (the paper's way of making extra operands) with their own values;
+    two-phase assembly, both phases timed (the symbolic one includes its host read of
+    nnz(A)); binary32 and binary64; A checked in full against the oracle."""
+    import torch
+    import oracle
+    import spd_synth
+    import paper_2207_13901_gb300 as spd
+    t0 = time.time()
+    n = A.nrows
+    ops = [A, spd_synth.shifted_csr(A, 1, seed=11), spd_synth.shifted_csr(A, 2, seed=12)]
+    nin = sum(M.nnz for M in ops)
+    out = {"inputs_nnz": nin, "generate_s": round(time.time() - t0, 1)}
+    for name, dt in (("f32", torch.float32), ("f64", torch.float64)):
+        d = [spd.CSR.from_host(M.pos, M.crd, M.vals, (n, n), dtype=dt) for M in ops]
+        s = d[0].vals.element_size()
+        R = spd.spadd3(*d)  # warm-up, and the result checked below
+        ms_total = _time_ms(lambda: spd.spadd3(*d), reps=5, warm=1)
+        sym = spd.spadd3_symbolic(*d)
+        ms_sym = _time_ms(lambda: spd.spadd3_symbolic(*d), reps=5, warm=1)
+        ms_num = _time_ms(lambda: spd.spadd3_numeric(sym, *d), reps=5, warm=1)
+        nnz_a = R.nnz
+        nbytes = 3 * 4 * (n + 1) + (4 + s) * nin + 4 * (n + 1) + (4 + R.vals.element_size()) * nnz_a
+        e = _entry(ms_total, nin, nbytes, hbm)
+        e["nnz_A"] = nnz_a
+        e["symbolic_ms"] = round(ms_sym, 3)  # counts, scans and the host read of nnz(A)
+        e["numeric_ms"] = round(ms_num, 3)
+        rops = [spd_synth.CSR(n, n, M.pos, M.crd, _rounded(M.vals, dt)) for M in ops]
+        ap, ac, av = oracle.spadd3(*rops)
+        _, _, sc = oracle.spadd3(*[spd_synth.CSR(n, n, M.pos, M.crd, np.abs(M.vals)) for M in rops])
+        e["structure_bit_exact"] = bool(np.array_equal(R.pos.cpu().numpy(), ap) and np.array_equal(R.crd.cpu().numpy(), ac))
+        e["error"] = error_stats(R.vals.double().cpu().numpy(), av, sc)
+        out["spadd3_" + name] = e
+        del d, R
+        torch.cuda.empty_cache()
+    return out
+
+
+def row_banded(hbm):
+    """SpMV on a banded matrix of about 700 million nonzeros (21.2M rows, 33 per row):
+    the synthetic workload of the paper's weak-scaling study, with perfect locality of
+    the x gathers, so it bounds the HBM fraction the SpMV kernel can reach."""
+    import torch
+    import oracle
+    import spd_synth
+    import paper_2207_13901_gb300 as spd
+    t0 = time.time()
+    n, w = 21_212_122, 16
+    A = spd_synth.banded_csr(n, w, seed=0, value_dtype=np.float32)
+    x = spd_synth.uniform(n, seed=2, dtype=np.float32)
+    out = {"nrows": n, "half_width": w, "nnz": A.nnz, "generate_s": round(time.time() - t0, 1)}
+    rng = np.random.default_rng(5)
+    sel = np.unique(np.concatenate([rng.integers(0, n, 2000), [0, n - 1]]))
+    # the sampled rows as their own CSR (the oracle then reads only those rows)
+    lens = (A.pos[sel + 1] - A.pos[sel]).astype(np.int64)
+    spos = np.concatenate([[0], np.cumsum(lens)]).astype(np.int32)
+    idx = np.concatenate([np.arange(A.pos[r], A.pos[r + 1]) for r in sel])
+    scrd, svals = A.crd[idx], A.vals[idx].astype(np.float64)
+    for name, dt in (("f32", torch.float32), ("f64", torch.float64), ("bf16", torch.bfloat16)):
+        dA = spd.CSR.from_host(A.pos, A.crd, A.vals, (n, n), dtype=dt)
+        xd = torch.from_numpy(x).cuda().to(dt)
+        y = torch.empty(n, dtype=spd.result_dtype(dt), device="cuda")
+        s = dA.vals.element_size()
+        for split in ("nnz", "row"):
+            ms = _time_ms(lambda: spd.spmv(dA, xd, y, split=split), reps=10)
+            e = _entry(ms, A.nnz, algorithmic_bytes("spmv", n, A.nnz, s, s, y.element_size()), hbm)
+            vr, xr = _rounded(svals, dt), _rounded(x.astype(np.float64), dt)
+            ref = oracle.spmv(spos, scrd, vr, xr, accurate=True)
+            sc = oracle.spmv(spos, scrd, np.abs(vr), np.abs(xr))
+            e["error"] = error_stats(y[torch.from_numpy(sel).cuda()].double().cpu().numpy(), ref, sc)
+            out["spmv_%s_%s" % (name, split)] = e
+        del dA, xd, y
+        torch.cuda.empty_cache()
+    out["wall_s"] = round(time.time() - t0, 1)
     return out
 
 

@@ -244,6 +244,40 @@ spd_status spd_csr_transpose(const spd_csr *A, int32_t *t_pos, int32_t *t_crd, i
  * Carries A's values into A^T's order. Asynchronous. */
 spd_status spd_gather_vals(int64_t n, const int32_t *perm, const void *in, void *out, int vtype, void *stream);
 
+/* -------------------------------------------------------------------- SpAdd3
+ *
+ * SpAdd3 A(i,j) = B(i,j) + C(i,j) + D(i,j) (Section VI-A): B, C, D are CSR of one shape
+ * and value type, each row with ascending distinct columns. A's pattern is the union
+ * of the three patterns (a coordinate stored in any operand is stored in A, even where
+ * the values cancel), so A is assembled in two phases (Section V-B): the symbolic call
+ * counts each row of A and writes A's pos; the caller then provides crd/vals of the
+ * returned size to the numeric call, which fills them. A value is (B + C) + D over the
+ * operands that store the coordinate, in binary64 for binary64 operands and in binary32
+ * otherwise; A's values have result type (SPD_F64 for F64, SPD_F32 otherwise).
+ * split: SPD_SPLIT_ROW (the rows in P = row_pieces or about (nrows + nnz) / unit_items
+ * pieces) or SPD_SPLIT_NNZ (pieces of unit_items of the fused rows, entries of B, C and
+ * D together; default 64; a piece inside a row takes a column range). Both calls must
+ * get the same operands, split, tuning and workspace; the workspace keeps the
+ * partition between them and must not be touched in between. */
+
+/* Workspace bytes of the two SpAdd3 calls (host only). */
+spd_status spd_spadd3_workspace_size(const spd_csr *B, const spd_csr *C, const spd_csr *D, int split,
+                                     const spd_tune *tune, size_t *bytes);
+
+/* Phase 1: a_pos (device int32[nrows + 1], caller-owned) receives A's pos; *nnz_out (host)
+ * receives nnz(A) = a_pos[nrows]. Synchronizes `stream` (the size is needed on the host
+ * to allocate A). nnz(B) + nnz(C) + nnz(D) must be below 2^31 - 1. */
+spd_status spd_spadd3_symbolic(const spd_csr *B, const spd_csr *C, const spd_csr *D, int split,
+                               const spd_tune *tune, int32_t *a_pos, int64_t *nnz_out, void *ws,
+                               size_t ws_bytes, void *stream);
+
+/* Phase 2: writes A's a_nnz coordinates into a_crd (device int32) and values into a_vals
+ * (device, a_type = result type), rows in order, columns ascending. a_pos is the
+ * symbolic call's output. Asynchronous. */
+spd_status spd_spadd3_numeric(const spd_csr *B, const spd_csr *C, const spd_csr *D, int split,
+                              const spd_tune *tune, const int32_t *a_pos, int64_t a_nnz, int32_t *a_crd,
+                              void *a_vals, int a_type, void *ws, size_t ws_bytes, void *stream);
+
 /* SDDMM A(i,j) = B(i,j) * C(i,k) * D(k,j), k < K. The output keeps B's pattern
  * (Section V-B): out_vals[p] is the value at B's position p, and B's pos/crd serve as
  * the output's. B->vals may be NULL: every B value is then 1 (the sampling pattern).

@@ -1,15 +1,16 @@
 """GB300-native sparse tensor algebra kernels of SpDISTAL (arXiv 2207.13901).
 
-SpMV, SpMM, SpMM^T, SDDMM, SpTTV and SpMTTKRP over CSR {Dense, Compressed} and CSF
+SpMV, SpMM, SpMM^T, SpAdd3, SDDMM, SpTTV and SpMTTKRP over CSR {Dense, Compressed} and CSF
 {Dense, Compressed, Compressed} operands, split by rows (universe partition) or by
 nonzeros (coordinate fusion + non-zero partition), executed by hand-written sm_103a
 kernels behind the C ABI of include/spd.h. PyTorch supplies memory and streams.
 """
 from .ops import (CSF3, CSR, CSRTranspose, csf3_workspace_size, csr_workspace_size, gather_vals, partition,
-                  result_dtype, sddmm, spmm, spmm_t, spmttkrp, spmv, spttv, transpose, validate)
+                  result_dtype, sddmm, spadd3, spadd3_numeric, spadd3_symbolic, spmm, spmm_t, spmttkrp, spmv, spttv, transpose, validate)
 from . import autograd, batched
 from .batched import SpMMBatch
 
 __all__ = ["CSR", "CSF3", "CSRTranspose", "spmv", "spmm", "spmm_t", "sddmm", "spttv", "spmttkrp", "validate",
-           "partition", "transpose", "gather_vals",
+           "partition", "transpose", "gather_vals", "spadd3", "spadd3_symbolic",
+           "spadd3_numeric",
            "csr_workspace_size", "csf3_workspace_size", "result_dtype", "autograd", "batched", "SpMMBatch"]

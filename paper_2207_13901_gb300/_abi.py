@@ -93,6 +93,9 @@ SIGNATURES = {
     "spd_csr_transpose_workspace_size": (_I, [_CSR, ctypes.POINTER(ctypes.c_size_t)]),
     "spd_csr_transpose": (_I, [_CSR, _P, _P, _P, _P, _SZ, _P]),
     "spd_gather_vals": (_I, [_I64, _P, _P, _P, _I, _P]),
+    "spd_spadd3_workspace_size": (_I, [_CSR, _CSR, _CSR, _I, _TUNE, ctypes.POINTER(ctypes.c_size_t)]),
+    "spd_spadd3_symbolic": (_I, [_CSR, _CSR, _CSR, _I, _TUNE, _P, ctypes.POINTER(ctypes.c_int64), _P, _SZ, _P]),
+    "spd_spadd3_numeric": (_I, [_CSR, _CSR, _CSR, _I, _TUNE, _P, _I64, _P, _P, _I, _P, _SZ, _P]),
     "spd_sddmm": (_I, [_CSR, _P, _I64, _I64, _P, _I64, _I, _P, _I, _I, _TUNE, _P, _SZ, _P]),
     "spd_spttv": (_I, [_CSF, _P, _I, _P, _I, _I, _TUNE, _P, _SZ, _P]),
     "spd_spmttkrp": (_I, [_CSF, _P, _I64, _P, _I64, _I64, _I, _P, _I64, _I, _I, _TUNE, _P, _SZ, _P]),

@@ -337,6 +337,11 @@ struct SpmmShape {
 SpmmShape pick_spmm_shape(int64_t L, size_t in_size, size_t out_size, const void *in, int64_t ld_in,
                           const void *out, int64_t ld_out, int lane_groups, uint64_t x_bytes);
 
+// Device-wide exclusive prefix sum of N int32 values in place (three launches on
+// `st`); `sums` holds scan_tile_count(N) ints of scratch.
+int64_t scan_tile_count(int64_t N);
+spd_status exclusive_scan_i32(int32_t *data, int64_t N, int32_t *sums, cudaStream_t st);
+
 // Zero rows x L of a row-major matrix with leading dimension lda (one warp per row).
 template <typename OT>
 __global__ void zero_rows_kernel(int64_t rows, int64_t L, OT *__restrict__ A, int64_t lda) {

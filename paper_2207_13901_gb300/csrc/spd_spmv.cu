@@ -3,10 +3,14 @@
 // is one output entry (the output keeps B's (i,j) structure, Section V-B).
 //
 // One thread block consumes one piece of the flattened coordinate tree, tile by tile:
-//   1. the tile's row-end offsets are staged in shared memory and its products
-//      vals[p] * x[crd[p]] are computed with coalesced crd/vals loads and x gathers;
-//   2. every thread takes IPT consecutive items of the tile (a merge-path search in
-//      shared memory gives its start), sums products and writes the rows it completes;
+//   1. each row whose end item falls in the tile sets that item's bit in a shared
+//      bitmap of the tile (item index = nonzeros before the row end + earlier row
+//      ends); a popcount prefix over the bitmap words gives, for any item, the number
+//      of row ends before it, i.e. where the merge path crosses that item. The tile's
+//      products vals[p] * x[crd[p]] are computed with coalesced crd/vals loads and x
+//      gathers into shared memory;
+//   2. every thread takes IPT consecutive items of the tile (its start row is one
+//      popcount away), sums products and writes the rows it completes;
 //   3. a block-wide segmented scan hands each thread the partial sum of the row it
 //      started in, and carries the open row into the next tile (compensated when a
 //      row spans tiles, i.e. is longer than one tile).
@@ -23,17 +27,6 @@ namespace spd {
 // 32/IPT banks.
 __device__ __forceinline__ int skew(int i) { return i + (i >> 5); }
 
-// Number of rows q < nr whose end item s_end[q] + q lies before item k.
-__device__ __forceinline__ int merge_count(const int32_t *s_end, int nr, int k) {
-    int lo = 0, hi = nr < k ? nr : k;
-    while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        if (s_end[skew(mid)] + mid < k) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
-}
-
 template <typename VT, int NT, int IPT>
 __global__ void __launch_bounds__(NT, sizeof(VT) == 8 ? 6 : 8) spmv_tile_kernel(
     int64_t n, const int32_t *__restrict__ pos, const int32_t *__restrict__ crd, const VT *__restrict__ vals,
@@ -45,8 +38,11 @@ __global__ void __launch_bounds__(NT, sizeof(VT) == 8 ? 6 : 8) spmv_tile_kernel(
     using OT = typename Traits<VT>::out;
     constexpr int TILE = NT * IPT;
     constexpr int NW = NT / 32;
+    constexpr int NWORDS = TILE / 32;  // bitmap words of a tile
     constexpr unsigned FULL = 0xffffffffu;
-    __shared__ int32_t s_end[TILE + TILE / 32];
+    static_assert(32 % IPT == 0 && NWORDS == 64, "a thread's items share one bitmap word; warp 0 scans 64 words");
+    __shared__ uint32_t s_bits[NWORDS];     // bit k of the tile: item k is a row end
+    __shared__ int32_t s_wpre[NWORDS + 1];  // row ends before each word; [NWORDS] = all
     __shared__ AT s_prod[TILE + TILE / 32];
     __shared__ AT s_wv[NW];
     __shared__ int s_wf[NW];
@@ -76,9 +72,27 @@ __global__ void __launch_bounds__(NT, sizeof(VT) == 8 ? 6 : 8) spmv_tile_kernel(
         if (rem_rows + rem_nnz == 0) break;
         const int nr = (int)(rem_rows < TILE ? rem_rows : TILE);
         const int items = (int)((rem_rows + rem_nnz) < TILE ? (rem_rows + rem_nnz) : TILE);
-        for (int q = tid; q < nr; q += NT) s_end[skew(q)] = ld_stream(pos + r + 1 + q) - p;
+        for (int w = tid; w < NWORDS; w += NT) s_bits[w] = 0u;
         __syncthreads();
-        const int ic = merge_count(s_end, nr, items);
+        for (int q = tid; q < nr; q += NT) {
+            const int e = ld_stream(pos + r + 1 + q) - p + q;  // item index of row q's end
+            if (e < items) atomicOr(&s_bits[e >> 5], 1u << (e & 31));
+        }
+        __syncthreads();
+        if (wid == 0) {  // exclusive popcount prefix of the 64 words, two per lane
+            const int c0 = __popc(s_bits[2 * lane]), c1 = __popc(s_bits[2 * lane + 1]);
+            int inc = c0 + c1;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int t = __shfl_up_sync(FULL, inc, off);
+                if (lane >= off) inc += t;
+            }
+            s_wpre[2 * lane] = inc - c0 - c1;
+            s_wpre[2 * lane + 1] = inc - c1;
+            if (lane == 31) s_wpre[NWORDS] = inc;
+        }
+        __syncthreads();
+        const int ic = s_wpre[NWORDS];  // row ends in the tile
         const int jc = items - ic;
         // products of the tile's nonzeros: coalesced crd/vals, gathered x
         {
@@ -100,14 +114,18 @@ __global__ void __launch_bounds__(NT, sizeof(VT) == 8 ? 6 : 8) spmv_tile_kernel(
         // this thread's IPT items of the tile
         const int k0 = tid * IPT < items ? tid * IPT : items;
         const int k1 = k0 + IPT < items ? k0 + IPT : items;
-        int i = merge_count(s_end, nr, k0);
+        const int word = k0 < TILE ? (k0 >> 5) : NWORDS - 1;
+        const int sh = k0 & 31;
+        const uint32_t wbits = s_bits[word];
+        const uint32_t mine = k0 < TILE ? wbits >> sh : 0u;  // bit k: item k0 + k is a row end
+        int i = s_wpre[word] + __popc(sh ? (wbits & ((1u << sh) - 1u)) : 0u);
         int j = k0 - i;
         AT acc = 0, first_val = 0;
         int first_row = -1;
 #pragma unroll
         for (int k = 0; k < IPT; ++k) {
             if (k0 + k < k1) {
-                if (i < nr && s_end[skew(i)] <= j) {  // row i ends here: all its children consumed
+                if ((mine >> k) & 1u) {  // row i ends here: all its children consumed
                     if (first_row < 0) {
                         first_row = i;
                         first_val = acc;

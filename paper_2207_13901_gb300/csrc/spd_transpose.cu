@@ -104,8 +104,11 @@ __global__ void __launch_bounds__(kSortThreads) scan_apply_kernel(int32_t *__res
     scan_block_items(data, N, (int64_t)blockIdx.x * kScanTile, sums[blockIdx.x], s_warp);
 }
 
-// In-place exclusive prefix sum of N int32 values (the total must fit in int32).
-static spd_status exclusive_scan(int32_t *data, int64_t N, int32_t *sums, cudaStream_t st) {
+// In-place exclusive prefix sum of N int32 values (the total must fit in int32); sums
+// holds scan_tile_count(N) ints.
+int64_t scan_tile_count(int64_t N) { return ceil_div(N, kScanTile) + 1; }
+
+spd_status exclusive_scan_i32(int32_t *data, int64_t N, int32_t *sums, cudaStream_t st) {
     if (N == 0) return SPD_OK;
     const int64_t nt = ceil_div(N, kScanTile);
     scan_tile_sum_kernel<<<(unsigned)nt, kSortThreads, 0, st>>>(data, N, sums);
@@ -252,7 +255,7 @@ static TransposeLayout transpose_layout(int64_t N) {
     T.hist = off;
     off += align_up(sizeof(int32_t) * (size_t)(T.nhist > 0 ? T.nhist : 1));
     T.sums = off;
-    off += align_up(sizeof(int32_t) * (size_t)(ceil_div(T.nhist, kScanTile) + 1));
+    off += align_up(sizeof(int32_t) * (size_t)scan_tile_count(T.nhist));
     T.total = off;
     return T;
 }
@@ -316,7 +319,7 @@ spd_status spd_csr_transpose(const spd_csr *A, int32_t *t_pos, int32_t *t_crd, i
             int32_t *vout = ((P - 1 - i) % 2 == 0) ? perm : pay;
             radix_hist_kernel<<<(unsigned)T.ntiles, kSortThreads, 0, st>>>(N, kin, 8 * i, hist, T.ntiles);
             if ((s = check_launch("radix_hist_kernel"))) return s;
-            if ((s = exclusive_scan(hist, T.nhist, sums, st))) return s;
+            if ((s = exclusive_scan_i32(hist, T.nhist, sums, st))) return s;
             radix_scatter_kernel<<<(unsigned)T.ntiles, kSortThreads, 0, st>>>(N, kin, vin, 8 * i, hist, T.ntiles,
                                                                               kout, vout);
             if ((s = check_launch("radix_scatter_kernel"))) return s;

@@ -361,6 +361,60 @@ def gather_vals(perm: torch.Tensor, vals: torch.Tensor, out: Optional[torch.Tens
     return out
 
 
+class Spadd3Symbolic:
+    """Result of SpAdd3's symbolic phase: A's pos, nnz(A) and the workspace (holding the
+    partition) that the numeric phase reads."""
+
+    def __init__(self, a_pos, nnz, ws, nbytes, split, tune):
+        self.a_pos, self.nnz, self.ws, self.nbytes, self.split, self.tune = a_pos, nnz, ws, nbytes, split, tune
+
+
+def spadd3_symbolic(B: CSR, C: CSR, D: CSR, split="nnz", tune=None, stream=None) -> Spadd3Symbolic:
+    """Phase 1 of A = B + C + D: count each row of A (the union of the three patterns)
+    and form A's pos; synchronizes the stream to return nnz(A)."""
+    lib = _abi.load()
+    for M in (C, D):
+        if M.shape != B.shape or M.dtype != B.dtype:
+            raise ValueError("B, C and D must share shape and value type")
+    n = B.shape[0]
+    dev = B.pos.device
+    st = _stream(stream)
+    d = [M.desc() for M in (B, C, D)]
+    dp = [ctypes.byref(x) for x in d]
+    nb = ctypes.c_size_t(0)
+    _abi.check("spd_spadd3_workspace_size", lib.spd_spadd3_workspace_size(*dp, _split(split), _tune(tune), ctypes.byref(nb)))
+    # a workspace of its own: it must survive, untouched, until the numeric phase
+    nbytes = max(int(nb.value), 1)
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    a_pos = torch.empty(n + 1, dtype=torch.int32, device=dev)
+    nnz = ctypes.c_int64(0)
+    _abi.check("spd_spadd3_symbolic", lib.spd_spadd3_symbolic(*dp, _split(split), _tune(tune), _ptr(a_pos),
+                                                              ctypes.byref(nnz), _ptr(ws), nbytes, st))
+    return Spadd3Symbolic(a_pos, int(nnz.value), ws, nbytes, split, tune)
+
+
+def spadd3_numeric(sym: Spadd3Symbolic, B: CSR, C: CSR, D: CSR, stream=None) -> CSR:
+    """Phase 2 of A = B + C + D: fill A's crd and vals (sizes from the symbolic phase)."""
+    lib = _abi.load()
+    dev = B.pos.device
+    d = [M.desc() for M in (B, C, D)]
+    dp = [ctypes.byref(x) for x in d]
+    a_crd = torch.empty(sym.nnz, dtype=torch.int32, device=dev)
+    a_vals = torch.empty(sym.nnz, dtype=result_dtype(B.dtype), device=dev)
+    _abi.check("spd_spadd3_numeric", lib.spd_spadd3_numeric(*dp, _split(sym.split), _tune(sym.tune), _ptr(sym.a_pos),
+                                                            sym.nnz, _ptr(a_crd), _ptr(a_vals), _code(a_vals.dtype),
+                                                            _ptr(sym.ws), sym.nbytes, _stream(stream)))
+    return CSR(sym.a_pos, a_crd, a_vals, B.shape)
+
+
+def spadd3(B: CSR, C: CSR, D: CSR, split="nnz", tune=None, stream=None) -> CSR:
+    """A = B + C + D on CSR operands of one shape and value type. A's pattern is the union
+    of the three (two-phase assembly: row counts and pos first, then crd and vals); the
+    call synchronizes the stream once, to learn nnz(A) before allocating it."""
+    sym = spadd3_symbolic(B, C, D, split=split, tune=tune, stream=stream)
+    return spadd3_numeric(sym, B, C, D, stream=stream)
+
+
 def sddmm(B: CSR, C: torch.Tensor, Dnk: torch.Tensor, out: Optional[torch.Tensor] = None, split="nnz", tune=None,
           ws=None, stream=None):
     """A(i,j) = B(i,j) C(i,k) D(k,j) on B's pattern; Dnk[j,k] = D(k,j). B.vals None => 1.

@@ -111,6 +111,28 @@ def test_transpose_host_checks():
     assert lib.spd_gather_vals(0, None, None, None, _abi.SPD_F32, None) == 0  # nothing to do
 
 
+def test_spadd3_host_checks():
+    lib = _abi.load()
+    size = ctypes.c_size_t(0)
+    A = _csr(nrows=1000, ncols=1000, nnz=20000)
+    assert lib.spd_spadd3_workspace_size(ctypes.byref(A), ctypes.byref(A), ctypes.byref(A), 1, None,
+                                         ctypes.byref(size)) == 0
+    assert size.value >= 4 * 1001 + 2 * 4 * (-(-(1000 + 60000) // 64) + 1)  # pos_sum and the partition
+    other = _csr(nrows=1000, ncols=999, nnz=20000)
+    assert lib.spd_spadd3_workspace_size(ctypes.byref(A), ctypes.byref(other), ctypes.byref(A), 1, None,
+                                         ctypes.byref(size)) == 2
+    f64 = _csr(nrows=1000, ncols=1000, nnz=20000, vtype=_abi.SPD_F64)
+    assert lib.spd_spadd3_workspace_size(ctypes.byref(A), ctypes.byref(A), ctypes.byref(f64), 1, None,
+                                         ctypes.byref(size)) == 3
+    nnz = ctypes.c_int64(0)
+    assert lib.spd_spadd3_symbolic(ctypes.byref(A), ctypes.byref(A), ctypes.byref(A), 1, None, None,
+                                   ctypes.byref(nnz), None, 0, None) == 1
+    assert lib.spd_spadd3_symbolic(ctypes.byref(A), ctypes.byref(A), ctypes.byref(A), 1, None, 4096,
+                                   ctypes.byref(nnz), None, 0, None) == 6
+    assert lib.spd_spadd3_numeric(ctypes.byref(A), ctypes.byref(A), ctypes.byref(A), 1, None, 4096, 10, 8192,
+                                  12288, _abi.SPD_F64, None, 0, None) == 3  # binary32 operands give binary32
+
+
 def test_product_path_has_no_oracle_dependency():
     """The package never imports or loads the oracle (no CPU fallback)."""
     pkg = os.path.join(ROOT, "paper_2207_13901_gb300")

@@ -68,6 +68,7 @@ def matrices():
         "empty_rows": small_csr(rng, 5000, 300, 0.002, empty_frac=0.9),
         "no_nnz": spd_synth.csr_from_coords(37, 20, [], [], vals=np.zeros(0)),
         "one_row": small_csr(rng, 1, 9000, 0.6, empty_frac=0.0),
+        "banded": spd_synth.banded_csr(20000, 16, seed=4),
     }
     return mats
 
@@ -82,7 +83,7 @@ def get_mats():
     return MATS
 
 
-MAT_NAMES = ["uniform4096", "rmat12", "longrow", "col0", "empty_rows", "no_nnz", "one_row"]
+MAT_NAMES = ["uniform4096", "rmat12", "longrow", "col0", "empty_rows", "no_nnz", "one_row", "banded"]
 
 
 def check(got, ref, scale, dtype, what):
