@@ -614,11 +614,14 @@ def row_spadd3(A, hbm):
         e["symbolic_ms"] = round(ms_sym, 3)  # counts, scans and the host read of nnz(A)
         e["numeric_ms"] = round(ms_num, 3)
         rops = [spd_synth.CSR(n, n, M.pos, M.crd, _rounded(M.vals, dt)) for M in ops]
+        t = time.perf_counter()
         ap, ac, av = oracle.spadd3(*rops)
+        t_oracle = time.perf_counter() - t
         _, _, sc = oracle.spadd3(*[spd_synth.CSR(n, n, M.pos, M.crd, np.abs(M.vals)) for M in rops])
         e["structure_bit_exact"] = bool(np.array_equal(R.pos.cpu().numpy(), ap) and np.array_equal(R.crd.cpu().numpy(), ac))
         e["error"] = error_stats(R.vals.double().cpu().numpy(), av, sc)
         out["spadd3_" + name] = e
+        out["oracle"] = {"nnz_per_s": nin / t_oracle, "cores": 1, "sample": "the whole problem, binary64"}
         del d, R
         torch.cuda.empty_cache()
     return out
@@ -659,6 +662,12 @@ def row_banded(hbm):
             out["spmv_%s_%s" % (name, split)] = e
         del dA, xd, y
         torch.cuda.empty_cache()
+    x64 = x.astype(np.float64)
+    t = time.perf_counter()
+    for _ in range(20):
+        oracle.spmv(spos, scrd, svals, x64)
+    out["oracle"] = {"nnz_per_s": 20 * scrd.shape[0] / (time.perf_counter() - t), "cores": 1,
+                     "sample": "%d rows (%d nonzeros), binary64" % (sel.size, scrd.shape[0])}
     out["wall_s"] = round(time.time() - t0, 1)
     return out
 
@@ -758,6 +767,11 @@ def row_backward(A, X32, hbm):
     sc = oracle.spmm(t_pos, t_crd, np.abs(vr), np.abs(Wh), sel=jsel)
     gx = Xd.grad.double().cpu().numpy()[jsel]
     out["spmm_t_dX_transpose"]["error"] = error_stats(gx, ref, sc)
+    t = time.perf_counter()
+    oracle.spmm(t_pos, t_crd, vr, Wh, sel=jsel)
+    onnz = int(np.diff(t_pos)[jsel].sum())
+    out["oracle"] = {"nnz_per_s": onnz / (time.perf_counter() - t), "cores": 1,
+                     "sample": "dX rows %d (%d nonzeros of A^T), binary64" % (jsel.size, onnz)}
     del dA, vals, Xd, W
     torch.cuda.empty_cache()
     return out
@@ -865,6 +879,15 @@ def row_batched(hbm):
         out[name] = e
         del dmats, Xs, batch
         torch.cuda.empty_cache()
+    # the oracle on whole matrices of the batch (one thread)
+    t = time.perf_counter()
+    onnz = 0
+    for m in check:
+        A = mats[m]
+        oracle.spmm(A.pos, A.crd, A.vals, Xh[m].astype(np.float64))
+        onnz += A.nnz
+    out["oracle"] = {"nnz_per_s": onnz / (time.perf_counter() - t), "cores": 1,
+                     "sample": "%d whole matrices of the batch, binary64" % len(check)}
     return out
 
 

@@ -61,7 +61,8 @@ __device__ __forceinline__ int32_t row_boundary(const Csr3 &m, int64_t r, int64_
             glen = l;
         }
     }
-    return m.crd[g][gb + (int32_t)((t * glen) / len)];
+    const int32_t *gc = g == 0 ? m.crd[0] : (g == 1 ? m.crd[1] : m.crd[2]);  // no indexing by a variable
+    return gc[gb + (int32_t)((t * glen) / len)];
 }
 
 template <typename VT>
@@ -69,11 +70,58 @@ __device__ __forceinline__ typename Traits<VT>::acc val_at(const void *v, int32_
     return (typename Traits<VT>::acc)to_acc(static_cast<const VT *>(v)[p]);
 }
 
+// Output writer of the numeric phase. A thread's outputs form one contiguous run of A
+// (its piece's); writing them one by one leaves 32-byte sectors partly written while
+// thousands of other runs compete for L2, so each thread gathers the outputs of one
+// aligned group of 8 positions in its own shared-memory slots and writes the group out
+// as whole sectors (vector stores) when it is complete, element by element otherwise.
+template <typename OT>
+struct GroupWriter {
+    int32_t *s_c;  // this thread's 8 slots
+    OT *s_v;
+    int32_t *a_crd;
+    OT *a_val;
+    int64_t first;  // first position written into the current group
+    bool vec;       // a_crd / a_val allow aligned 32-byte (crd) and 8-element (vals) groups
+
+    __device__ __forceinline__ void flush(int64_t last) {  // positions [first, last] of one group
+        const int64_t g0 = last & ~int64_t(7);
+        if (vec && first == g0 && last == g0 + 7) {
+            const int4 *c4 = reinterpret_cast<const int4 *>(s_c);
+            int4 *dc = reinterpret_cast<int4 *>(a_crd + g0);
+            dc[0] = c4[0];
+            dc[1] = c4[1];
+            if constexpr (sizeof(OT) == 4) {
+                const float4 *v4 = reinterpret_cast<const float4 *>(s_v);
+                float4 *dv = reinterpret_cast<float4 *>(a_val + g0);
+                dv[0] = v4[0];
+                dv[1] = v4[1];
+            } else {
+                const double2 *v2 = reinterpret_cast<const double2 *>(s_v);
+                double2 *dv = reinterpret_cast<double2 *>(a_val + g0);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) dv[q] = v2[q];
+            }
+        } else {
+            for (int64_t g = first; g <= last; ++g) {
+                a_crd[g] = s_c[g & 7];
+                a_val[g] = s_v[g & 7];
+            }
+        }
+        first = last + 1;
+    }
+    __device__ __forceinline__ void put(int64_t g, int32_t j, OT v, int64_t end) {
+        s_c[g & 7] = j;
+        s_v[g & 7] = v;
+        if ((g & 7) == 7 || g == end - 1) flush(g);
+    }
+};
+
 // Merges the part of piece c that lies in row r, columns [vlo, vhi); returns the number
-// of A entries produced. NUMERIC: write them from out[k0] on.
+// of A entries produced. NUMERIC: hands them to the writer from position k0 on.
 template <typename VT, bool NUMERIC>
-__device__ int64_t merge_row(const Csr3 &m, int64_t r, int32_t vlo, int32_t vhi, int32_t *a_crd,
-                             typename Traits<VT>::out *a_val, int64_t k0) {
+__device__ __forceinline__ int64_t merge_row(const Csr3 &m, int64_t r, int32_t vlo, int32_t vhi,
+                             GroupWriter<typename Traits<VT>::out> *wr, int64_t k0, int64_t kend) {
     using AT = typename Traits<VT>::acc;
     int32_t p[3], e[3];
 #pragma unroll
@@ -103,10 +151,7 @@ __device__ int64_t merge_row(const Csr3 &m, int64_t r, int32_t vlo, int32_t vhi,
                 c[q] = p[q] < e[q] ? m.crd[q][p[q]] : INT32_MAX;
             }
         }
-        if (NUMERIC) {
-            a_crd[k0 + k] = j;
-            a_val[k0 + k] = (typename Traits<VT>::out)v;
-        }
+        if (NUMERIC) wr->put(k0 + k, j, (typename Traits<VT>::out)v, kend);
         ++k;
     }
     return k;
@@ -114,17 +159,33 @@ __device__ int64_t merge_row(const Csr3 &m, int64_t r, int32_t vlo, int32_t vhi,
 
 // One thread per piece of the fused tree (rows r0 .. r1 with item offsets p0, p1 into
 // pos_sum). SYMBOLIC (NUMERIC = false): adds each row's union count to a_pos[r] and
-// stores the piece's total in piece_cnt[c]. NUMERIC: writes from piece_start[c] on.
+// stores the piece's total in piece_cnt[c]. NUMERIC: writes positions
+// [piece_start[c], piece_start[c + 1]).
 template <typename VT, bool NUMERIC>
 __global__ void __launch_bounds__(kSpadd3Threads) spadd3_kernel(
-    int64_t n, int64_t ncols, Csr3 m, const int32_t *__restrict__ psum, const int32_t *__restrict__ prow,
+    int64_t n, Csr3 m, const int32_t *__restrict__ psum, const int32_t *__restrict__ prow,
     const int32_t *__restrict__ ppos, int64_t npieces, int64_t P, int32_t *__restrict__ a_pos,
     int32_t *__restrict__ piece_cnt, const int32_t *__restrict__ piece_start, int32_t *__restrict__ a_crd,
-    typename Traits<VT>::out *__restrict__ a_val) {
+    typename Traits<VT>::out *__restrict__ a_val, bool vec) {
+    using OT = typename Traits<VT>::out;
+    __shared__ __align__(16) int32_t s_c[NUMERIC ? kSpadd3Threads * 8 : 1];
+    __shared__ __align__(16) OT s_v[NUMERIC ? kSpadd3Threads * 8 : 1];
+    const int64_t np = prow ? npieces : P;
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= (prow ? npieces : P)) return;
+    if (c >= np) return;
     const PieceBounds b = prow ? nnz_piece(c, prow, ppos) : row_piece(c, P, n, psum);
-    int64_t k = NUMERIC ? (int64_t)piece_start[c] : 0;
+    GroupWriter<OT> wr;
+    int64_t k = 0, kend = 0;
+    if (NUMERIC) {
+        wr.s_c = s_c + threadIdx.x * 8;
+        wr.s_v = s_v + threadIdx.x * 8;
+        wr.a_crd = a_crd;
+        wr.a_val = a_val;
+        wr.vec = vec;
+        k = piece_start[c];
+        kend = piece_start[c + 1];
+        wr.first = k;
+    }
     int64_t total = 0;
     for (int64_t r = b.r0; r <= b.r1 && r < n; ++r) {
         const int64_t base = psum[r], len = (int64_t)psum[r + 1] - base;
@@ -134,12 +195,15 @@ __global__ void __launch_bounds__(kSpadd3Threads) spadd3_kernel(
         const int32_t vlo = ts > 0 ? row_boundary(m, r, ts, len) : INT32_MIN;
         const int32_t vhi = te < len ? row_boundary(m, r, te, len) : INT32_MAX;
         if (vlo >= vhi) continue;  // the range lies inside one column's run: a later piece owns it
-        const int64_t cnt = merge_row<VT, NUMERIC>(m, r, vlo, vhi, a_crd, a_val, k);
+        const int64_t cnt = merge_row<VT, NUMERIC>(m, r, vlo, vhi, &wr, k, kend);
         if (!NUMERIC && cnt) atomicAdd(a_pos + r, (int32_t)cnt);
         k += cnt;
         total += cnt;
     }
-    if (!NUMERIC) piece_cnt[c] = (int32_t)total;
+    if (!NUMERIC) {
+        piece_cnt[c] = (int32_t)total;
+        if (c == np - 1) piece_cnt[np] = 0;  // the scan then leaves the total at [np]
+    }
 }
 
 // Workspace: pos_sum, the partition, the per-piece counts/starts and the scan's tile
@@ -209,12 +273,13 @@ static spd_status launch_spadd3(const spd_csr *B, const Csr3 &m, const Spadd3Lay
     using OT = typename Traits<VT>::out;
     const int64_t work = L.npieces;
     const unsigned grid = (unsigned)ceil_div(work > 0 ? work : 1, kSpadd3Threads);
+    const bool vec = a_crd && a_val && aligned(a_crd, 32) && aligned(a_val, 8 * sizeof(OT));
     spadd3_kernel<VT, NUMERIC><<<grid, kSpadd3Threads, 0, st>>>(
-        B->nrows, B->ncols, m, reinterpret_cast<const int32_t *>(w + L.psum),
+        B->nrows, m, reinterpret_cast<const int32_t *>(w + L.psum),
         nnz_split ? reinterpret_cast<const int32_t *>(w + L.prow) : nullptr,
         nnz_split ? reinterpret_cast<const int32_t *>(w + L.ppos) : nullptr, L.npieces, L.P, a_pos,
         reinterpret_cast<int32_t *>(w + L.pcnt), reinterpret_cast<const int32_t *>(w + L.pcnt), a_crd,
-        static_cast<OT *>(a_val));
+        static_cast<OT *>(a_val), vec);
     return check_launch(NUMERIC ? "spadd3_kernel(numeric)" : "spadd3_kernel(symbolic)");
 }
 
@@ -279,7 +344,7 @@ spd_status spd_spadd3_symbolic(const spd_csr *B, const spd_csr *C, const spd_csr
         }
         if (s) return s;
         // piece counts -> piece starts; row counts -> A's pos
-        if ((s = exclusive_scan_i32(reinterpret_cast<int32_t *>(w + L.pcnt), L.npieces, sums, st))) return s;
+        if ((s = exclusive_scan_i32(reinterpret_cast<int32_t *>(w + L.pcnt), L.npieces + 1, sums, st))) return s;
     }
     if ((s = exclusive_scan_i32(a_pos, n + 1, sums, st))) return s;
     int32_t total = 0;
