@@ -64,6 +64,7 @@ _SIGS = {
     "orc_csr_transpose": [_I64, _I64, _P, _P, _P, _P, _P],
     "orc_spadd3_count": [_I64, _P, _P, _P, _P, _P, _P, _P],
     "orc_spadd3": [_I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P],
+    "orc_column_blocks": [_I64, _P, _P, _I64, _P, _P, _P, _P],
 }
 
 
@@ -164,6 +165,19 @@ def spadd3(B, C, D):
     lib().orc_spadd3(n, *[_ptr(a) for t in ops for a in t], _ptr(ap), _ptr(ac), _ptr(av))
     nnz = int(ap[-1])
     return ap, ac[:nnz].copy(), av[:nnz].copy()
+
+
+def column_blocks(pos, crd, bounds):
+    """Value-range blocks of A's columns: (blk_pos [nblk, n+1], blk_crd, perm, blk_nnz)."""
+    pos, crd, bounds = _i32(pos), _i32(crd), _i32(bounds)
+    n = pos.shape[0] - 1
+    nblk = bounds.shape[0] - 1
+    blk_pos = np.zeros((nblk, n + 1), dtype=np.int32)
+    blk_crd = np.zeros(max(crd.shape[0], 1), dtype=np.int32)
+    perm = np.zeros(max(crd.shape[0], 1), dtype=np.int32)
+    lib().orc_column_blocks(n, _ptr(pos), _ptr(crd), nblk, _ptr(bounds), _ptr(blk_pos), _ptr(blk_crd), _ptr(perm))
+    total = int(blk_pos[:, -1].sum())
+    return blk_pos, blk_crd[:total].copy(), perm[:total].copy(), blk_pos[:, -1].astype(np.int64)
 
 
 def validate_level(nparent: int, nchild_dim: int, pos, crd):

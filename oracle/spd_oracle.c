@@ -482,3 +482,32 @@ void orc_spadd3(int64_t n, const int32_t *bp, const int32_t *bc, const double *b
         ap[i + 1] = (int32_t)(ap[i] + k);
     }
 }
+
+/* ------------------------------------------------------------------------------------
+ * Universe partition of the Compressed level by coordinate value ranges (the Compressed
+ * row of the partitioning table, Section IV-B: partitionByValueRanges on crd, then the
+ * preimage in pos). Block b holds A's entries whose column lies in
+ * [bounds[b], bounds[b+1]); it is written as its own CSR (the same {Dense, Compressed}
+ * format): pos at blk_pos + b*(n+1), coordinates at blk_crd + off_b where off_b is the
+ * number of entries of earlier blocks, and perm (same offsets) giving each entry's
+ * position in A. Blocks are filled block by block, rows ascending, positions ascending.
+ * ------------------------------------------------------------------------------------ */
+void orc_column_blocks(int64_t n, const int32_t *pos, const int32_t *crd, int64_t nblk,
+                       const int32_t *bounds, int32_t *blk_pos, int32_t *blk_crd, int32_t *perm) {
+    int64_t out = 0;
+    for (int64_t b = 0; b < nblk; ++b) {
+        int32_t *bp = blk_pos + b * (n + 1);
+        int64_t k = 0;
+        bp[0] = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            for (int64_t p = pos[i]; p < pos[i + 1]; ++p)
+                if (crd[p] >= bounds[b] && crd[p] < bounds[b + 1]) {
+                    blk_crd[out + k] = crd[p];
+                    perm[out + k] = (int32_t)p;
+                    ++k;
+                }
+            bp[i + 1] = (int32_t)k;
+        }
+        out += k;
+    }
+}

@@ -104,6 +104,14 @@ def test_golden_spadd3():
     assert np.array_equal(av, g["a_vals"])
 
 
+def test_golden_column_blocks():
+    g = read_golden("column_blocks_4x5.txt")
+    blk_pos, blk_crd, perm, nnz = oracle.column_blocks(g["pos"], g["crd"], g["bounds"])
+    assert np.array_equal(blk_pos[0], g["blk_pos0"]) and np.array_equal(blk_pos[1], g["blk_pos1"])
+    assert np.array_equal(blk_crd, g["blk_crd"]) and np.array_equal(perm, g["perm"])
+    assert np.array_equal(nnz, g["blk_nnz"])
+
+
 # ------------------------------------------------------------------------------ dense brute force
 
 @pytest.mark.parametrize("seed", SEEDS)
@@ -479,6 +487,36 @@ def test_spadd3_against_scipy():
     ap, ac, av = oracle.spadd3(*ops)
     assert np.array_equal(ap, R.indptr) and np.array_equal(ac, R.indices)
     assert np.array_equal(av, R.data)
+
+
+# ------------------------------------------------------------------------------ column blocks
+
+@pytest.mark.parametrize("seed", SEEDS)
+def test_column_blocks_partition_the_matrix(seed):
+    """The blocks' dense forms add up to A, every block holds only its columns, the
+    permutation covers A once, and each row's split points are numpy's searchsorted of
+    the bounds in that row; SpMM over the blocks sums to SpMM over A (exact on integers)."""
+    rng = np.random.default_rng(seed)
+    A = small_csr(rng, 41, 37, 0.2, long_rows=1, integer=True)
+    bounds = np.array([0, 5, 6, 20, 37], dtype=np.int32)
+    blk_pos, blk_crd, perm, nnz = oracle.column_blocks(A.pos, A.crd, bounds)
+    assert np.array_equal(np.sort(perm), np.arange(A.nnz))
+    off = np.concatenate([[0], np.cumsum(nnz)])
+    total = np.zeros((41, 37))
+    X = rng.integers(-4, 5, (37, 3)).astype(np.float64)
+    Y = np.zeros((41, 3))
+    for b in range(4):
+        c = blk_crd[off[b]:off[b + 1]]
+        assert np.all((c >= bounds[b]) & (c < bounds[b + 1]))
+        Ab = spd_synth.CSR(41, 37, blk_pos[b], c, A.vals[perm[off[b]:off[b + 1]]])
+        total += dense_of_csr(Ab)
+        Y += oracle.spmm(Ab.pos, Ab.crd, Ab.vals, X)
+        for i in range(41):
+            row = A.crd[A.pos[i]:A.pos[i + 1]]
+            lo, hi = np.searchsorted(row, [bounds[b], bounds[b + 1]])
+            assert blk_pos[b][i + 1] - blk_pos[b][i] == hi - lo
+    assert np.array_equal(total, dense_of_csr(A))
+    assert np.array_equal(Y, oracle.spmm(A.pos, A.crd, A.vals, X))
 
 
 # ------------------------------------------------------------------------------ library cross-check
