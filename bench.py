@@ -55,7 +55,7 @@ def parse_args(argv=None):
     p.add_argument("--fixed-tune", default="",
                    help="UNIT,BLOCK,INFLIGHT: skip the autotuner and run SpMM with this tuning (nnz split)")
     p.add_argument("--rows", default="all",
-                   help="comma list of extra hot-path rows to measure: cfg1,sddmm,backward,csf,batched,banded,spadd3 "
+                   help="comma list of extra hot-path rows to measure: cfg1,sddmm,backward,csf,batched,banded,spadd3,colblock "
                         "(or all, none)")
     return p.parse_args(argv)
 
@@ -443,12 +443,12 @@ def run_gpu(args):
         cpu = cpu_baseline(A, x32, X32, args.cpu_budget)
 
     rows_out = {}
-    wanted = {"cfg1", "sddmm", "backward", "csf", "batched", "banded", "spadd3"} if args.rows == "all" else \
+    wanted = {"cfg1", "sddmm", "backward", "csf", "batched", "banded", "spadd3", "colblock"} if args.rows == "all" else \
         (set() if args.rows == "none" else set(args.rows.split(",")))
     for name, fn in (("cfg1", lambda: row_cfg1(hbm)), ("backward", lambda: row_backward(A, X32, hbm)),
                      ("sddmm", lambda: row_sddmm(hbm)), ("csf", lambda: row_csf(hbm)),
                      ("batched", lambda: row_batched(hbm)), ("banded", lambda: row_banded(hbm)),
-                     ("spadd3", lambda: row_spadd3(A, hbm))):
+                     ("spadd3", lambda: row_spadd3(A, hbm)), ("colblock", lambda: row_colblock(A, X32, hbm))):
         if name not in wanted:
             continue
         if name == "backward":
@@ -623,6 +623,47 @@ def row_spadd3(A, hbm):
         out["spadd3_" + name] = e
         out["oracle"] = {"nnz_per_s": nin / t_oracle, "cores": 1, "sample": "the whole problem, binary64"}
         del d, R
+        torch.cuda.empty_cache()
+    return out
+
+
+def row_colblock(A, X32, hbm):
+    """SpMM (L = 128, binary32) over value-range column blocks of A (a universe partition
+    of the Compressed level) against the plain SpMM, on two matrices: the 2^22 R-MAT
+    (square: every block costs a pass over Y as large as X) and a wide 2^18 x 2^23 matrix
+    with 256 uniform columns per row (X is 4.3 GB, Y 134 MB: blocks of X fit in L2 and
+    the extra passes over Y are cheap)."""
+    import torch
+    import oracle
+    import spd_synth
+    import paper_2207_13901_gb300 as spd
+    t0 = time.time()
+    W = spd_synth.uniform_csr(1 << 18, 1 << 23, 256, seed=9)
+    XW = spd_synth.uniform((W.ncols, L_COLS), seed=10, dtype=np.float32)
+    out = {"wide": {"nrows": W.nrows, "ncols": W.ncols, "nnz": W.nnz}, "generate_s": round(time.time() - t0, 1)}
+    rng = np.random.default_rng(8)
+    for name, M, Xh, blocks in (("rmat22", A, X32, (4, 32)), ("wide", W, XW, (16, 64))):
+        dM = spd.CSR.from_host(M.pos, M.crd, M.vals, (M.nrows, M.ncols), dtype=torch.float32)
+        Xd = torch.from_numpy(Xh).cuda()
+        Y = torch.empty((M.nrows, L_COLS), dtype=torch.float32, device="cuda")
+        nb = 4 * (M.nrows + 1) + 8 * M.nnz + 4 * L_COLS * (M.ncols + M.nrows)  # X read once, Y written once
+        res = {"plain": _entry(_time_ms(lambda: spd.spmm(dM, Xd, Y), reps=5), M.nnz, nb, hbm)}
+        sel = np.unique(rng.integers(0, M.nrows, 300))
+        vr, Xr = _rounded(M.vals, torch.float32), Xh.astype(np.float64)
+        ref = oracle.spmm(M.pos, M.crd, vr, Xr, sel=sel, accurate=True)
+        sc = oracle.spmm(M.pos, M.crd, np.abs(vr), np.abs(Xr), sel=sel)
+        for nblk in blocks:
+            t = time.perf_counter()
+            spd.column_blocks(dM, nblk=nblk)
+            torch.cuda.synchronize()
+            build_ms = (time.perf_counter() - t) * 1e3
+            ms = _time_ms(lambda: spd.spmm_column_blocked(dM, Xd, Y, nblk=nblk), reps=5)
+            e = _entry(ms, M.nnz, nb, hbm)
+            e["blocks_build_ms"] = round(build_ms, 1)
+            e["error"] = error_stats(Y.double().cpu().numpy()[sel], ref, sc)
+            res["blocks%d" % nblk] = e
+        out[name] = dict(out.get(name, {}), **res)
+        del dM, Xd, Y
         torch.cuda.empty_cache()
     return out
 

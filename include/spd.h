@@ -205,6 +205,14 @@ spd_status spd_spmm(const spd_csr *A, const void *X, int64_t L, int64_t ldx, int
                     int64_t ldy, int y_type, int split, const spd_tune *tune, void *ws,
                     size_t ws_bytes, void *stream);
 
+/* Y(i,l) += A(i,j) * X(j,l): as spd_spmm, but the product is added to Y (the generated
+ * code's "+=" of Section IV-C on an output that already holds values). Rows of A without
+ * entries leave Y untouched. Used to sum the products of column blocks
+ * (spd_csr_column_blocks). */
+spd_status spd_spmm_accumulate(const spd_csr *A, const void *X, int64_t L, int64_t ldx, int x_type, void *Y,
+                               int64_t ldy, int y_type, int split, const spd_tune *tune, void *ws,
+                               size_t ws_bytes, void *stream);
+
 /* SpMM^T dX(j,l) = A(i,j) * dY(i,l): the gradient of Y = A X with respect to X, without
  * forming A's transpose (rows of A are walked and scattered with atomic adds, so the
  * summation order is not deterministic).  dY: nrows x L (ldy) of dy_type ==
@@ -243,6 +251,30 @@ spd_status spd_csr_transpose(const spd_csr *A, int32_t *t_pos, int32_t *t_crd, i
 /* out[q] = in[perm[q]] for q < n: n elements of vtype, device memory, caller-owned.
  * Carries A's values into A^T's order. Asynchronous. */
 spd_status spd_gather_vals(int64_t n, const int32_t *perm, const void *in, void *out, int vtype, void *stream);
+
+/* -------------------------------------------------------------------- column blocks
+ *
+ * Universe partition of A's Compressed level by coordinate value ranges (Section IV-B,
+ * the Compressed row of the partitioning table: partitionByValueRanges on crd and its
+ * preimage in pos). Block b holds A's entries with bounds[b] <= column < bounds[b+1] and
+ * is written as its own CSR of A's shape: pos at blk_pos + b*(nrows+1) (nrows+1 int32,
+ * starting at 0), coordinates at blk_crd + off_b, where off_b = blk_nnz[0] + ... +
+ * blk_nnz[b-1], and perm (same offsets) holding each entry's position in A, so that the
+ * block's values are vals[perm[...]] (spd_gather_vals). Entries keep A's row order and,
+ * within a row, column order. Y = A X is then the sum over blocks of A_b X, each of which
+ * gathers only rows bounds[b] .. bounds[b+1]-1 of X (spd_spmm for the first block,
+ * spd_spmm_accumulate for the others). */
+
+/* Workspace bytes of spd_csr_column_blocks (host only); 1 <= nblk <= 65536. */
+spd_status spd_csr_column_blocks_workspace_size(const spd_csr *A, int64_t nblk, size_t *bytes);
+
+/* bounds: host int32[nblk + 1], bounds[0] = 0, bounds[nblk] = ncols, non-decreasing.
+ * blk_pos: device int32[nblk * (nrows + 1)]; blk_crd, perm: device int32[nnz]; blk_nnz:
+ * host int64[nblk] (entries per block). A->vals is not read. Synchronizes `stream`
+ * (the block sizes are returned on the host). */
+spd_status spd_csr_column_blocks(const spd_csr *A, int64_t nblk, const int32_t *bounds, int32_t *blk_pos,
+                                 int32_t *blk_crd, int32_t *perm, int64_t *blk_nnz, void *ws, size_t ws_bytes,
+                                 void *stream);
 
 /* -------------------------------------------------------------------- SpAdd3
  *

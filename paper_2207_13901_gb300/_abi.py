@@ -89,10 +89,13 @@ SIGNATURES = {
     "spd_csr_partition": (_I, [_CSR, _I, _I64, _I64, _P, _P, _P]),
     "spd_spmv": (_I, [_CSR, _P, _I, _P, _I, _I, _TUNE, _P, _SZ, _P]),
     "spd_spmm": (_I, [_CSR, _P, _I64, _I64, _I, _P, _I64, _I, _I, _TUNE, _P, _SZ, _P]),
+    "spd_spmm_accumulate": (_I, [_CSR, _P, _I64, _I64, _I, _P, _I64, _I, _I, _TUNE, _P, _SZ, _P]),
     "spd_spmm_t": (_I, [_CSR, _P, _I64, _I64, _I, _P, _I64, _I, _I, _TUNE, _P, _SZ, _P]),
     "spd_csr_transpose_workspace_size": (_I, [_CSR, ctypes.POINTER(ctypes.c_size_t)]),
     "spd_csr_transpose": (_I, [_CSR, _P, _P, _P, _P, _SZ, _P]),
     "spd_gather_vals": (_I, [_I64, _P, _P, _P, _I, _P]),
+    "spd_csr_column_blocks_workspace_size": (_I, [_CSR, _I64, ctypes.POINTER(ctypes.c_size_t)]),
+    "spd_csr_column_blocks": (_I, [_CSR, _I64, _P, _P, _P, _P, _P, _P, _SZ, _P]),
     "spd_spadd3_workspace_size": (_I, [_CSR, _CSR, _CSR, _I, _TUNE, ctypes.POINTER(ctypes.c_size_t)]),
     "spd_spadd3_symbolic": (_I, [_CSR, _CSR, _CSR, _I, _TUNE, _P, ctypes.POINTER(ctypes.c_int64), _P, _SZ, _P]),
     "spd_spadd3_numeric": (_I, [_CSR, _CSR, _CSR, _I, _TUNE, _P, _I64, _P, _P, _I, _P, _SZ, _P]),

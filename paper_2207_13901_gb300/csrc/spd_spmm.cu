@@ -15,7 +15,7 @@ namespace spd {
 
 constexpr unsigned FULL = kFullMask;
 
-template <typename VT, int EPL, int G, int U, bool FULLTILE>
+template <typename VT, int EPL, int G, int U, bool FULLTILE, bool ACC>
 __global__ void __launch_bounds__(256, kSpmmMinBlocks) spmm_warp_kernel(
     int64_t n, const int32_t *__restrict__ pos, const int32_t *__restrict__ crd, const VT *__restrict__ vals,
     const VT *__restrict__ X, uint32_t ldx_bytes, typename Traits<VT>::out *__restrict__ Y, int64_t ldy, int64_t L,
@@ -35,12 +35,12 @@ __global__ void __launch_bounds__(256, kSpmmMinBlocks) spmm_warp_kernel(
     double *cval = carry_row ? carry_val + c * L : nullptr;
     if constexpr (G == 32) {
         const int64_t col = (int64_t)blockIdx.y * (32 * EPL) + (int64_t)lane * EPL;
-        spmm_piece<VT, EPL, U, FULLTILE>(n, pos, crd, vals, X, ldx_bytes, Y, ldy, L, b, col, lane, s_crd, s_val, crow,
+        spmm_piece<VT, EPL, U, FULLTILE, ACC>(n, pos, crd, vals, X, ldx_bytes, Y, ldy, L, b, col, lane, s_crd, s_val, crow,
                                          blockIdx.y == 0, cval);
     } else {
         const int64_t col = (int64_t)blockIdx.y * (G * EPL) + (int64_t)(lane % G) * EPL;
         AT *s_cmp = reinterpret_cast<AT *>(spmm_smem + wpb * 64 * sizeof(int32_t)) + wpb * 64 + wid * 32 * EPL;
-        spmm_piece_grouped<VT, EPL, G, U, FULLTILE>(n, pos, crd, vals, X, ldx_bytes, Y, ldy, L, b, col, lane, s_crd,
+        spmm_piece_grouped<VT, EPL, G, U, FULLTILE, ACC>(n, pos, crd, vals, X, ldx_bytes, Y, ldy, L, b, col, lane, s_crd,
                                                     s_val, s_cmp, crow, blockIdx.y == 0, cval);
     }
 }
@@ -113,7 +113,7 @@ static int64_t default_row_pieces(int64_t n, int64_t nnz, int64_t unit) {
     return P < 1 ? 1 : P;
 }
 
-template <typename VT, int EPL, int G, int U, bool FULLTILE>
+template <typename VT, int EPL, int G, int U, bool FULLTILE, bool ACC>
 static spd_status launch_spmm_shape(const spd_csr *A, const void *X, int64_t L, int64_t ldx, void *Y, int64_t ldy,
                                     int split, const Tuning &tn, void *ws, cudaStream_t st) {
     using OT = typename Traits<VT>::out;
@@ -126,7 +126,7 @@ static spd_status launch_spmm_shape(const spd_csr *A, const void *X, int64_t L, 
     if (split == SPD_SPLIT_ROW) {
         const int64_t P = tn.row_pieces > 0 ? tn.row_pieces : default_row_pieces(A->nrows, A->nnz, tn.unit_items);
         dim3 grid((unsigned)ceil_div(P, wpb), (unsigned)ctiles);
-        spmm_warp_kernel<VT, EPL, G, U, FULLTILE><<<grid, tn.block_threads, smem, st>>>(
+        spmm_warp_kernel<VT, EPL, G, U, FULLTILE, ACC><<<grid, tn.block_threads, smem, st>>>(
             A->nrows, A->pos, A->crd, v, x, (uint32_t)(ldx * sizeof(VT)), y, ldy, L, nullptr, nullptr, 0, P, nullptr,
             nullptr);
         return check_launch("spmm_warp_kernel(row)");
@@ -140,7 +140,7 @@ static spd_status launch_spmm_shape(const spd_csr *A, const void *X, int64_t L, 
     spd_status s = launch_merge_partition(A->nrows, A->nnz, A->pos, tn.unit_items, Lw.npieces, prow, ppos, st);
     if (s) return s;
     dim3 grid((unsigned)ceil_div(Lw.npieces, wpb), (unsigned)ctiles);
-    spmm_warp_kernel<VT, EPL, G, U, FULLTILE><<<grid, tn.block_threads, smem, st>>>(
+    spmm_warp_kernel<VT, EPL, G, U, FULLTILE, ACC><<<grid, tn.block_threads, smem, st>>>(
         A->nrows, A->pos, A->crd, v, x, (uint32_t)(ldx * sizeof(VT)), y, ldy, L, prow, ppos, Lw.npieces, 0, crow,
         cval);
     if ((s = check_launch("spmm_warp_kernel(nnz)"))) return s;
@@ -149,31 +149,32 @@ static spd_status launch_spmm_shape(const spd_csr *A, const void *X, int64_t L, 
 
 // Rows in flight per group: the tuning's 4 or 8 for one entry per warp step in the
 // binary32 modes; 4 for binary64 (8 would spill) and for lane groups.
-template <typename VT, int EPL, int G>
+template <typename VT, int EPL, int G, bool ACC>
 static spd_status launch_spmm_u(const spd_csr *A, const void *X, int64_t L, int64_t ldx, void *Y, int64_t ldy,
                                 int split, const Tuning &tn, void *ws, cudaStream_t st) {
     const bool full = L % (G * EPL) == 0;
     if constexpr (sizeof(VT) == 8 || G < 32) {
-        return full ? launch_spmm_shape<VT, EPL, G, 4, true>(A, X, L, ldx, Y, ldy, split, tn, ws, st)
-                    : launch_spmm_shape<VT, EPL, G, 4, false>(A, X, L, ldx, Y, ldy, split, tn, ws, st);
+        return full ? launch_spmm_shape<VT, EPL, G, 4, true, ACC>(A, X, L, ldx, Y, ldy, split, tn, ws, st)
+                    : launch_spmm_shape<VT, EPL, G, 4, false, ACC>(A, X, L, ldx, Y, ldy, split, tn, ws, st);
     } else {
         if (tn.inflight == 4)
-            return full ? launch_spmm_shape<VT, EPL, G, 4, true>(A, X, L, ldx, Y, ldy, split, tn, ws, st)
-                        : launch_spmm_shape<VT, EPL, G, 4, false>(A, X, L, ldx, Y, ldy, split, tn, ws, st);
-        return full ? launch_spmm_shape<VT, EPL, G, 8, true>(A, X, L, ldx, Y, ldy, split, tn, ws, st)
-                    : launch_spmm_shape<VT, EPL, G, 8, false>(A, X, L, ldx, Y, ldy, split, tn, ws, st);
+            return full ? launch_spmm_shape<VT, EPL, G, 4, true, ACC>(A, X, L, ldx, Y, ldy, split, tn, ws, st)
+                        : launch_spmm_shape<VT, EPL, G, 4, false, ACC>(A, X, L, ldx, Y, ldy, split, tn, ws, st);
+        return full ? launch_spmm_shape<VT, EPL, G, 8, true, ACC>(A, X, L, ldx, Y, ldy, split, tn, ws, st)
+                    : launch_spmm_shape<VT, EPL, G, 8, false, ACC>(A, X, L, ldx, Y, ldy, split, tn, ws, st);
     }
 }
 
 template <typename VT>
 static spd_status launch_spmm(const spd_csr *A, const void *X, int64_t L, int64_t ldx, void *Y, int64_t ldy,
-                              int split, const Tuning &tn, void *ws, cudaStream_t st) {
+                              int split, const Tuning &tn, void *ws, cudaStream_t st, bool accumulate) {
     using OT = typename Traits<VT>::out;
     const SpmmShape sh = pick_spmm_shape(L, sizeof(VT), sizeof(OT), X, ldx, Y, ldy, tn.lane_groups,
                                          (uint64_t)A->ncols * (uint64_t)ldx * sizeof(VT));
     return with_lane_shape<VT>(sh.epl, sh.group, [&](auto shape) {
         constexpr int E = decltype(shape)::epl, G = decltype(shape)::group;
-        return launch_spmm_u<VT, E, G>(A, X, L, ldx, Y, ldy, split, tn, ws, st);
+        return accumulate ? launch_spmm_u<VT, E, G, true>(A, X, L, ldx, Y, ldy, split, tn, ws, st)
+                          : launch_spmm_u<VT, E, G, false>(A, X, L, ldx, Y, ldy, split, tn, ws, st);
     });
 }
 
@@ -230,10 +231,10 @@ static spd_status launch_spmm_t(const spd_csr *A, const void *dY, int64_t L, int
 
 using namespace spd;
 
-extern "C" {
-
-spd_status spd_spmm(const spd_csr *A, const void *X, int64_t L, int64_t ldx, int x_type, void *Y, int64_t ldy,
-                    int y_type, int split, const spd_tune *tune, void *ws, size_t ws_bytes, void *stream) {
+// The two SpMM entry points: overwrite Y, or add to it.
+static spd_status spmm_entry(const spd_csr *A, const void *X, int64_t L, int64_t ldx, int x_type, void *Y, int64_t ldy,
+                             int y_type, int split, const spd_tune *tune, void *ws, size_t ws_bytes, void *stream,
+                             bool accumulate) {
     spd_status s = check_csr(A, true);
     if (s) return s;
     if (L < 0) return fail(SPD_ERR_SHAPE, "L %lld < 0", (long long)L);
@@ -252,11 +253,25 @@ spd_status spd_spmm(const spd_csr *A, const void *X, int64_t L, int64_t ldx, int
     if (A->nrows == 0 || L == 0) return SPD_OK;
     cudaStream_t st = as_stream(stream);
     switch (A->vtype) {
-        case SPD_F64: return launch_spmm<double>(A, X, L, ldx, Y, ldy, split, tn, ws, st);
-        case SPD_F32: return launch_spmm<float>(A, X, L, ldx, Y, ldy, split, tn, ws, st);
-        case SPD_BF16: return launch_spmm<__nv_bfloat16>(A, X, L, ldx, Y, ldy, split, tn, ws, st);
+        case SPD_F64: return launch_spmm<double>(A, X, L, ldx, Y, ldy, split, tn, ws, st, accumulate);
+        case SPD_F32: return launch_spmm<float>(A, X, L, ldx, Y, ldy, split, tn, ws, st, accumulate);
+        case SPD_BF16: return launch_spmm<__nv_bfloat16>(A, X, L, ldx, Y, ldy, split, tn, ws, st, accumulate);
         default: return fail(SPD_ERR_DTYPE, "unknown value type %d", A->vtype);
     }
+}
+
+extern "C" {
+
+
+spd_status spd_spmm(const spd_csr *A, const void *X, int64_t L, int64_t ldx, int x_type, void *Y, int64_t ldy,
+                    int y_type, int split, const spd_tune *tune, void *ws, size_t ws_bytes, void *stream) {
+    return spmm_entry(A, X, L, ldx, x_type, Y, ldy, y_type, split, tune, ws, ws_bytes, stream, false);
+}
+
+spd_status spd_spmm_accumulate(const spd_csr *A, const void *X, int64_t L, int64_t ldx, int x_type, void *Y,
+                               int64_t ldy, int y_type, int split, const spd_tune *tune, void *ws, size_t ws_bytes,
+                               void *stream) {
+    return spmm_entry(A, X, L, ldx, x_type, Y, ldy, y_type, split, tune, ws, ws_bytes, stream, true);
 }
 
 spd_status spd_spmm_t(const spd_csr *A, const void *dY, int64_t L, int64_t ldy, int dy_type, void *dX, int64_t ldx,

@@ -43,7 +43,9 @@ struct RowWindow {
 // One piece [b.r0, b.p0) -> [b.r1, b.p1) of matrix (n, pos, crd, vals) times X into Y.
 // s_crd / s_val: this warp's two 32-entry windows in shared memory. carry_row /
 // carry_val (nullable): where the partial of row b.r1 goes when the piece ends inside it.
-template <typename VT, int EPL, int U, bool FULLTILE>
+// ACC: add the product to Y (Y += A X) instead of overwriting it; rows of A without
+// entries leave Y untouched.
+template <typename VT, int EPL, int U, bool FULLTILE, bool ACC = false>
 __device__ __forceinline__ void spmm_piece(int64_t n, const int32_t *__restrict__ pos,
                                            const int32_t *__restrict__ crd, const VT *__restrict__ vals,
                                            const VT *__restrict__ X, uint32_t ldx_bytes,
@@ -71,10 +73,16 @@ __device__ __forceinline__ void spmm_piece(int64_t n, const int32_t *__restrict_
     bool kahan = (sizeof(AT) == 4) && (true_end - cur_start > kLongRow);
 
     auto emit = [&]() {
-        if (active) {
+        if (active && (!ACC || true_end > cur_start)) {
             OT o[EPL];
 #pragma unroll
             for (int e = 0; e < EPL; ++e) o[e] = (OT)(acc[e] - cmp[e]);
+            if constexpr (ACC) {
+                OT old[EPL];
+                ld_vec<EPL>(Y + (int64_t)r * ldy + col, old);
+#pragma unroll
+                for (int e = 0; e < EPL; ++e) o[e] = old[e] + o[e];
+            }
             st_vec(Y + (int64_t)r * ldy + col, o);
         }
         zero(acc);
@@ -229,7 +237,7 @@ struct XVec<__nv_bfloat16, EPL> {
 // (q % NG) * G + q / NG so that the U entries a group takes in one step are adjacent.
 // s_cmp: this warp's 32*EPL slots for the Kahan compensations of a long row (kept out of
 // registers, long rows being rare). Other arguments as for spmm_piece.
-template <typename VT, int EPL, int G, int U, bool FULLTILE>
+template <typename VT, int EPL, int G, int U, bool FULLTILE, bool ACC = false>
 __device__ __forceinline__ void spmm_piece_grouped(int64_t n, const int32_t *__restrict__ pos,
                                                    const int32_t *__restrict__ crd, const VT *__restrict__ vals,
                                                    const VT *__restrict__ X, uint32_t ldx_bytes,
@@ -280,10 +288,16 @@ __device__ __forceinline__ void spmm_piece_grouped(int64_t n, const int32_t *__r
                 for (int m = G; m < 32; m <<= 1) acc[e] += __shfl_xor_sync(kFullMask, acc[e], m);
             }
         }
-        if (writer) {
+        if (writer && (!ACC || true_end > cur_start)) {
             OT o[EPL];
 #pragma unroll
             for (int e = 0; e < EPL; ++e) o[e] = (OT)acc[e];
+            if constexpr (ACC) {
+                OT old[EPL];
+                ld_vec<EPL>(Y + (int64_t)r * ldy + col, old);
+#pragma unroll
+                for (int e = 0; e < EPL; ++e) o[e] = old[e] + o[e];
+            }
             st_vec(Y + (int64_t)r * ldy + col, o);
         }
         zero(acc);

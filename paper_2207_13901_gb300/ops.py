@@ -298,6 +298,96 @@ def spmm(A: CSR, X: torch.Tensor, Y: Optional[torch.Tensor] = None, split="nnz",
     return Y
 
 
+def spmm_accumulate(A: CSR, X: torch.Tensor, Y: torch.Tensor, split="nnz", tune=None, ws=None, stream=None):
+    """Y(i,l) += A(i,j) X(j,l) in place; rows of A without entries leave Y as it is."""
+    lib = _abi.load()
+    _cuda(X, "X")
+    _cuda(Y, "Y")
+    n, m = A.shape
+    if X.dim() != 2 or X.shape[0] != m or X.dtype != A.dtype or X.stride(1) != 1:
+        raise ValueError("X must be a row-major %d x L matrix of %s" % (m, A.dtype))
+    L = X.shape[1]
+    if Y.shape != (n, L) or Y.dtype != result_dtype(A.dtype) or Y.stride(1) != 1:
+        raise ValueError("Y must be a row-major %d x %d matrix of %s" % (n, L, result_dtype(A.dtype)))
+    st = _stream(stream)
+    need = csr_workspace_size(_abi.SPD_OP_SPMM, A, split, L, tune)
+    buf, nb = _ws(need, X.device, st, ws)
+    d = A.desc()
+    _abi.check("spd_spmm_accumulate", lib.spd_spmm_accumulate(ctypes.byref(d), _ptr(X), L, X.stride(0), _code(X.dtype),
+                                                              _ptr(Y), Y.stride(0), _code(Y.dtype), _split(split),
+                                                              _tune(tune), _ptr(buf), nb, st))
+    return Y
+
+
+class ColumnBlocks:
+    """A's column blocks (``spd_csr_column_blocks``): block b holds the entries with
+    bounds[b] <= column < bounds[b+1], as a CSR over blk_pos[b], the slice of blk_crd at
+    off[b], and perm into A's positions."""
+
+    def __init__(self, bounds, blk_pos, blk_crd, perm, nnz, shape):
+        self.bounds, self.blk_pos, self.blk_crd, self.perm, self.nnz, self.shape = bounds, blk_pos, blk_crd, perm, nnz, shape
+        self.off = [0]
+        for k in nnz:
+            self.off.append(self.off[-1] + k)
+
+    def matrices(self, vals: Optional[torch.Tensor], stream=None):
+        """The blocks as CSR matrices of A's shape carrying ``vals`` (A's values, A's order)."""
+        bv = None if vals is None else gather_vals(self.perm, vals, stream=stream)
+        out = []
+        for b in range(len(self.nnz)):
+            s, e = self.off[b], self.off[b + 1]
+            out.append(CSR(self.blk_pos[b], self.blk_crd[s:e], None if bv is None else bv[s:e], self.shape))
+        return out
+
+
+def column_blocks(A: CSR, nblk: Optional[int] = None, bounds=None, stream=None) -> ColumnBlocks:
+    """Split A's columns into value ranges (equal ranges when only nblk is given); cached
+    per pattern and bounds."""
+    lib = _abi.load()
+    n, m = A.shape
+    if bounds is None:
+        if not nblk or nblk < 1:
+            raise ValueError("give nblk >= 1 or bounds")
+        bounds = [(b * m) // nblk for b in range(nblk + 1)]
+    bounds = [int(v) for v in bounds]
+    key = ("column_blocks", tuple(bounds))
+    hit = A._structure_cache.get(key)
+    if hit is not None:
+        return hit
+    nb = len(bounds) - 1
+    dev = A.pos.device
+    st = _stream(stream)
+    d = A.desc()
+    size = ctypes.c_size_t(0)
+    _abi.check("spd_csr_column_blocks_workspace_size",
+               lib.spd_csr_column_blocks_workspace_size(ctypes.byref(d), nb, ctypes.byref(size)))
+    buf, nbytes = _ws(int(size.value), dev, st, None)
+    b_host = (ctypes.c_int32 * (nb + 1))(*bounds)
+    blk_pos = torch.empty((nb, n + 1), dtype=torch.int32, device=dev)
+    blk_crd = torch.empty(A.nnz, dtype=torch.int32, device=dev)
+    perm = torch.empty(A.nnz, dtype=torch.int32, device=dev)
+    counts = (ctypes.c_int64 * nb)()
+    _abi.check("spd_csr_column_blocks", lib.spd_csr_column_blocks(ctypes.byref(d), nb, b_host, _ptr(blk_pos),
+                                                                  _ptr(blk_crd), _ptr(perm), counts, _ptr(buf),
+                                                                  nbytes, st))
+    cb = ColumnBlocks(bounds, blk_pos, blk_crd, perm, [int(c) for c in counts], A.shape)
+    A._structure_cache[key] = cb
+    return cb
+
+
+def spmm_column_blocked(A: CSR, X: torch.Tensor, Y: Optional[torch.Tensor] = None, nblk: Optional[int] = None,
+                        bounds=None, split="nnz", tune=None, stream=None):
+    """Y = A X as the sum over A's column blocks of A_b X (the first block overwrites Y, the
+    others add to it): each product gathers only its block's slab of X."""
+    cb = column_blocks(A, nblk=nblk, bounds=bounds, stream=stream)
+    mats = cb.matrices(A.vals, stream=stream)
+    Y = spmm(mats[0], X, Y, split=split, tune=tune, stream=stream)
+    for Ab in mats[1:]:
+        if Ab.nnz:
+            spmm_accumulate(Ab, X, Y, split=split, tune=tune, stream=stream)
+    return Y
+
+
 def spmm_t(A: CSR, dY: torch.Tensor, dX: Optional[torch.Tensor] = None, split="nnz", tune=None, ws=None,
            stream=None, method: str = "atomic"):
     """dX(j,l) = A(i,j) dY(i,l): the gradient of Y = A X with respect to X.

@@ -133,6 +133,24 @@ def test_spadd3_host_checks():
                                   12288, _abi.SPD_F64, None, 0, None) == 3  # binary32 operands give binary32
 
 
+def test_column_block_host_checks():
+    lib = _abi.load()
+    size = ctypes.c_size_t(0)
+    A = _csr(nrows=1000, ncols=1000, nnz=20000)
+    assert lib.spd_csr_column_blocks_workspace_size(ctypes.byref(A), 4, ctypes.byref(size)) == 0
+    assert size.value > 0
+    assert lib.spd_csr_column_blocks_workspace_size(ctypes.byref(A), 0, ctypes.byref(size)) == 10
+    cnt = (ctypes.c_int64 * 4)()
+    bad_end = (ctypes.c_int32 * 5)(0, 10, 20, 30, 999)  # must end at ncols
+    assert lib.spd_csr_column_blocks(ctypes.byref(A), 4, bad_end, 4096, 8192, 12288, cnt, 1 << 20, 1 << 30, None) == 10
+    decreasing = (ctypes.c_int32 * 5)(0, 500, 400, 900, 1000)
+    assert lib.spd_csr_column_blocks(ctypes.byref(A), 4, decreasing, 4096, 8192, 12288, cnt, 1 << 20, 1 << 30, None) == 10
+    ok = (ctypes.c_int32 * 5)(0, 250, 500, 750, 1000)
+    assert lib.spd_csr_column_blocks(ctypes.byref(A), 4, ok, 4096, 8192, 12288, cnt, None, 0, None) == 6
+    # the accumulating SpMM checks its arguments like spd_spmm
+    assert lib.spd_spmm_accumulate(ctypes.byref(A), 4096, 8, 4, 1, 8192, 8, 1, 1, None, None, 0, None) == 2
+
+
 def test_product_path_has_no_oracle_dependency():
     """The package never imports or loads the oracle (no CPU fallback)."""
     pkg = os.path.join(ROOT, "paper_2207_13901_gb300")
