@@ -132,6 +132,49 @@ __device__ __forceinline__ void st_vec(double *p, const double (&v)[N]) {
     }
 }
 
+template <typename T, int N>
+__device__ __forceinline__ void zero(T (&a)[N]) {
+#pragma unroll
+    for (int e = 0; e < N; ++e) a[e] = (T)0;
+}
+
+// One lane's EPL elements of a dense row, as loaded by one vector access. bfloat16
+// elements stay packed two per register and are widened only when multiplied (exactly:
+// a bfloat16 is the upper half of the binary32 of the same value).
+template <typename VT, int EPL>
+struct XVec {
+    VT v[EPL];
+    __device__ __forceinline__ void load(const VT *p) { ld_vec<EPL>(p, v); }
+    __device__ __forceinline__ void clear() { zero(v); }
+    __device__ __forceinline__ VT at(int e) const { return v[e]; }
+};
+template <int EPL>
+struct XVec<__nv_bfloat16, EPL> {
+    static constexpr int W = EPL >= 2 ? EPL / 2 : 1;
+    uint32_t w[W];
+    __device__ __forceinline__ void load(const __nv_bfloat16 *p) {
+        if constexpr (EPL == 1) {
+            w[0] = (uint32_t)__bfloat16_as_ushort(__ldg(p));
+        } else if constexpr (EPL == 2) {
+            w[0] = __ldg(reinterpret_cast<const unsigned int *>(p));
+        } else if constexpr (EPL == 4) {
+            const uint2 r = __ldg(reinterpret_cast<const uint2 *>(p));
+            w[0] = r.x; w[1] = r.y;
+        } else {
+#pragma unroll
+            for (int q = 0; q < EPL / 8; ++q) {
+                const uint4 r = __ldg(reinterpret_cast<const uint4 *>(p) + q);
+                w[4 * q] = r.x; w[4 * q + 1] = r.y; w[4 * q + 2] = r.z; w[4 * q + 3] = r.w;
+            }
+        }
+    }
+    __device__ __forceinline__ void clear() { zero(w); }
+    __device__ __forceinline__ float at(int e) const {
+        const uint32_t x = w[e >> 1];
+        return __uint_as_float((e & 1) ? (x & 0xffff0000u) : (x << 16));
+    }
+};
+
 // Kahan's compensated accumulation of a product a*b: s carries the running sum and c the
 // negated rounding error of the additions so far (s - c approximates the exact sum).
 template <typename T>

@@ -150,16 +150,16 @@ __global__ void __launch_bounds__(256) spmttkrp_warp_kernel(
             if (seg != cs) finish_to(seg);
 #pragma unroll 1
             for (int t0 = a; t0 < bnd; t0 += NPG * U) {
-                AT cv[U][EPL], dv[U][EPL];
+                XVec<VT, EPL> cv[U], dv[U];  // bfloat16 stays packed until the multiply
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     const int j = t0 + u * NPG + gi;
                     if (active && j < bnd) {
-                        ld_vec<EPL>(C + (int64_t)s_j[j] * ldc + col, cv[u]);
-                        ld_vec<EPL>(D + (int64_t)s_k[j] * ldd + col, dv[u]);
+                        cv[u].load(C + (int64_t)s_j[j] * ldc + col);
+                        dv[u].load(D + (int64_t)s_k[j] * ldd + col);
                     } else {
-#pragma unroll
-                        for (int e = 0; e < EPL; ++e) cv[u][e] = dv[u][e] = 0;
+                        cv[u].clear();
+                        dv[u].clear();
                     }
                 }
 #pragma unroll
@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(256) spmttkrp_warp_kernel(
                     const int j = t0 + u * NPG + gi;
                     const AT v = j < bnd ? s_v[j] : (AT)0;
 #pragma unroll
-                    for (int e = 0; e < EPL; ++e) acc[e] = fma(v * cv[u][e], dv[u][e], acc[e]);
+                    for (int e = 0; e < EPL; ++e) acc[e] = fma(v * (AT)cv[u].at(e), (AT)dv[u].at(e), acc[e]);
                 }
             }
             dirty = true;

@@ -73,22 +73,22 @@ __global__ void __launch_bounds__(256) sddmm_warp_kernel(
             for (int64_t kt = 0; kt < ktiles; ++kt) {
                 const int64_t k = kt * (G * EPL) + (int64_t)gl * EPL;
                 if (k < K) {
-                    AT cv[U][EPL], dv[U][EPL];
+                    XVec<VT, EPL> cv[U], dv[U];  // bfloat16 stays packed until the multiply
 #pragma unroll
                     for (int u = 0; u < U; ++u) {
                         const int j = j0 + u * NPG + gi;
                         if (j < cnt) {
-                            ld_vec<EPL>(C + (int64_t)s_row[j] * ldc + k, cv[u]);
-                            ld_vec<EPL>(Dnk + (int64_t)s_crd[j] * ldd + k, dv[u]);
+                            cv[u].load(C + (int64_t)s_row[j] * ldc + k);
+                            dv[u].load(Dnk + (int64_t)s_crd[j] * ldd + k);
                         } else {
-#pragma unroll
-                            for (int e = 0; e < EPL; ++e) cv[u][e] = dv[u][e] = 0;
+                            cv[u].clear();
+                            dv[u].clear();
                         }
                     }
 #pragma unroll
                     for (int u = 0; u < U; ++u) {
 #pragma unroll
-                        for (int e = 0; e < EPL; ++e) part[u] = fma(cv[u][e], dv[u][e], part[u]);
+                        for (int e = 0; e < EPL; ++e) part[u] = fma((AT)cv[u].at(e), (AT)dv[u].at(e), part[u]);
                     }
                 }
             }
