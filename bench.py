@@ -109,6 +109,12 @@ def workload(scale: int):
     return A, x, X, time.time() - t0
 
 
+def workload_name(scale: int) -> str:
+    """The benchmarked workload, named the same way by both arms."""
+    return ("SpMV + SpMM(L=128) on R-MAT 2^%d (a=.57,b=.19,c=.19, 16 samples/row, dedup), binary32, nnz split "
+            "(fused non-zero partition), step = partition + SpMV + fix-up + SpMM + fix-up" % scale)
+
+
 def algorithmic_bytes(kernel: str, n: int, nnz: int, vbytes: int, xbytes: int, ybytes: int, L: int = L_COLS) -> int:
     """Bytes every kernel must move at least once: pos, crd, values, the dense input
     read once and the output written once."""
@@ -506,9 +512,7 @@ def run_gpu(args):
             "dtype": "f32",
             "data": "synthetic",
             "config": {
-                "workload": "SpMV + SpMM(L=128) on R-MAT 2^%d (a=.57,b=.19,c=.19, 16 samples/row, dedup), "
-                            "binary32, nnz split (fused non-zero partition), step = partition + SpMV + fix-up + "
-                            "SpMM + fix-up" % args.scale,
+                "workload": workload_name(args.scale),
                 "nrows": n, "nnz": nnz, "L": L_COLS, "split": {"spmv": sp_v, "spmm": sp_m},
                 "tune": {"spmv": tu_v, "spmm": tu_m},
                 "units": "nonzeros processed (2 x nnz per step)",
@@ -1025,7 +1029,9 @@ def run_reference(args):
         "impl": "reference", "metric": "nonzeros/s", "value": value, "unit": "nnz/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "SpMV + SpMM(L=128) on R-MAT 2^%d, CPU oracle on a row sample" % args.scale},
+        "config": {"workload": workload_name(args.scale), "nrows": A.nrows, "nnz": A.nnz, "L": L_COLS,
+                   "units": "nonzeros processed (2 x nnz per step)",
+                   "reference": "the CPU oracle (binary64, one thread) on a row sample of the workload: " + sample},
         "cpu_baseline": {"value": value, "unit": "nnz/s", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "nnz/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
