@@ -414,8 +414,26 @@ __global__ void carry_fixup_rows_kernel(int64_t npieces, int64_t L, const int32_
     const int32_t row = carry_row[c];
     if (row < 0) return;
     if (c > 0 && carry_row[c - 1] == row) return;
+    // The run of pieces that ended inside this row is walked 8 pieces at a time, with
+    // the 8 row tags and then the 8 carries loaded together: a row spanning a hundred
+    // pieces costs a dozen memory round trips, not a hundred. Summation stays in piece
+    // order.
     double s = 0.0;
-    for (int64_t d = c; d < npieces && carry_row[d] == row; ++d) s += carry_val[d * L + col];
+    for (int64_t d = c; d < npieces; d += 8) {
+        int32_t tag[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) tag[k] = d + k < npieces ? carry_row[d + k] : -1;
+        double v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = tag[k] == row ? carry_val[(d + k) * L + col] : 0.0;
+        bool more = true;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            more = more && tag[k] == row;
+            if (more) s += v[k];
+        }
+        if (!more) break;
+    }
     OT *yp = Y + (int64_t)row * ldy + col;
     *yp = (OT)((double)*yp + s);
 }

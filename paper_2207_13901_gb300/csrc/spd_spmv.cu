@@ -221,8 +221,22 @@ __global__ void carry_fixup_scalar_kernel(int64_t npieces, const int32_t *__rest
     int32_t row = carry_row[c];
     if (row < 0) return;
     if (c > 0 && carry_row[c - 1] == row) return;
-    double s = 0.0;
-    for (int64_t d = c; d < npieces && carry_row[d] == row; ++d) s += carry_val[d];
+    double s = 0.0;  // the run in batches of 8 independent loads, summed in piece order
+    for (int64_t d = c; d < npieces; d += 8) {
+        int32_t tag[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) tag[k] = d + k < npieces ? carry_row[d + k] : -1;
+        double v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = tag[k] == row ? carry_val[d + k] : 0.0;
+        bool more = true;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            more = more && tag[k] == row;
+            if (more) s += v[k];
+        }
+        if (!more) break;
+    }
     y[row] = (OT)((double)y[row] + s);
 }
 
