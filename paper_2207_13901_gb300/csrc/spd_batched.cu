@@ -99,21 +99,7 @@ __global__ void spmm_batched_fixup_kernel(const BatchDesc *__restrict__ descs, c
     if (row < 0) return;
     if (c > 0 && cr[c - 1] == row) return;
     double s = 0.0;
-    for (int64_t e = c; e < d.P; e += 8) {  // the run in batches of 8 independent loads, in piece order
-        int32_t tag[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) tag[k] = e + k < d.P ? cr[e + k] : -1;
-        double v[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) v[k] = tag[k] == row ? cv[(e + k) * L + col] : 0.0;
-        bool more = true;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            more = more && tag[k] == row;
-            if (more) s += v[k];
-        }
-        if (!more) break;
-    }
+    for (int64_t e = c; e < d.P && cr[e] == row; ++e) s += cv[e * L + col];
     OT *yp = static_cast<OT *>(d.Y) + (int64_t)row * d.ldy + col;
     *yp = (OT)((double)*yp + s);
 }

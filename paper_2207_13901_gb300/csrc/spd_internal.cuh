@@ -405,45 +405,73 @@ inline spd_status launch_zero_rows(int64_t rows, int64_t L, OT *A, int64_t lda, 
 // Adds the binary64 carries of consecutive pieces that ended inside the same outer entry
 // (row or slice) to the value the completing piece wrote. One warp per piece, one lane
 // per column; only the first piece of each run does the work.
-template <typename OT>
+// Adds the binary64 carries of consecutive pieces that ended inside the same row to the
+// row the completing piece wrote: one warp per piece (only the first piece of a run
+// works), each lane EPL consecutive columns (vector loads of the carries and of Y).
+template <typename OT, int EPL>
 __global__ void carry_fixup_rows_kernel(int64_t npieces, int64_t L, const int32_t *__restrict__ carry_row,
                                         const double *__restrict__ carry_val, OT *__restrict__ Y, int64_t ldy) {
     const int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int64_t col = (int64_t)blockIdx.y * 32 + (threadIdx.x & 31);
+    const int64_t col = ((int64_t)blockIdx.y * 32 + (threadIdx.x & 31)) * EPL;
     if (c >= npieces || col >= L) return;
     const int32_t row = carry_row[c];
     if (row < 0) return;
     if (c > 0 && carry_row[c - 1] == row) return;
-    // The run of pieces that ended inside this row is walked 8 pieces at a time, with
-    // the 8 row tags and then the 8 carries loaded together: a row spanning a hundred
-    // pieces costs a dozen memory round trips, not a hundred. Summation stays in piece
-    // order.
-    double s = 0.0;
-    for (int64_t d = c; d < npieces; d += 8) {
-        int32_t tag[8];
+    double s[EPL];
+    ld_vec<EPL>(carry_val + c * L + col, s);
+    if (c + 1 < npieces && carry_row[c + 1] == row) {
+        // a row spanning many pieces: its run is walked 8 pieces at a time, the 8 row tags
+        // loaded together and then the carries 4 at a time (about 36 round trips for
+        // ~100 pieces instead of ~100); the sum still runs in piece order
+        for (int64_t d = c + 1; d < npieces; d += 8) {
+            int32_t tag[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) tag[k] = d + k < npieces ? carry_row[d + k] : -1;
-        double v[8];
+            for (int k = 0; k < 8; ++k) tag[k] = d + k < npieces ? carry_row[d + k] : -1;
+            bool more = true;
+#pragma unroll 1
+            for (int h = 0; h < 8 && more; h += 4) {  // 4 carries in flight at a time
+                double v[4][EPL];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) v[k] = tag[k] == row ? carry_val[(d + k) * L + col] : 0.0;
-        bool more = true;
+                for (int k = 0; k < 4; ++k) {
+                    if (tag[h + k] == row) {
+                        ld_vec<EPL>(carry_val + (d + h + k) * L + col, v[k]);
+                    } else {
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            more = more && tag[k] == row;
-            if (more) s += v[k];
+                        for (int e = 0; e < EPL; ++e) v[k][e] = 0.0;
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    more = more && tag[h + k] == row;
+                    if (more) {
+#pragma unroll
+                        for (int e = 0; e < EPL; ++e) s[e] += v[k][e];
+                    }
+                }
+            }
+            if (!more) break;
         }
-        if (!more) break;
     }
     OT *yp = Y + (int64_t)row * ldy + col;
-    *yp = (OT)((double)*yp + s);
+    OT o[EPL];
+    ld_vec<EPL>(yp, o);
+#pragma unroll
+    for (int e = 0; e < EPL; ++e) o[e] = (OT)((double)o[e] + s[e]);
+    st_vec(yp, o);
 }
 
 template <typename OT>
 inline spd_status launch_carry_fixup(int64_t npieces, int64_t L, const int32_t *crow, const double *cval, OT *Y,
                                      int64_t ldy, cudaStream_t st) {
     if (npieces <= 0 || L <= 0) return SPD_OK;
-    dim3 grid((unsigned)ceil_div(npieces, 8), (unsigned)ceil_div(L, 32));
-    carry_fixup_rows_kernel<OT><<<grid, 256, 0, st>>>(npieces, L, crow, cval, Y, ldy);
+    const bool vec4 = L % 4 == 0 && ldy % 4 == 0 && aligned(Y, 4 * sizeof(OT)) && aligned(cval, 32);
+    if (vec4) {
+        dim3 grid((unsigned)ceil_div(npieces, 8), (unsigned)ceil_div(L, 128));
+        carry_fixup_rows_kernel<OT, 4><<<grid, 256, 0, st>>>(npieces, L, crow, cval, Y, ldy);
+    } else {
+        dim3 grid((unsigned)ceil_div(npieces, 8), (unsigned)ceil_div(L, 32));
+        carry_fixup_rows_kernel<OT, 1><<<grid, 256, 0, st>>>(npieces, L, crow, cval, Y, ldy);
+    }
     return check_launch("carry_fixup_rows_kernel");
 }
 
