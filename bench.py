@@ -109,6 +109,12 @@ def workload(scale: int):
     return A, x, X, time.time() - t0
 
 
+# Binary64 fused multiply-add peak of this GPU: 152 SMs x 2 binary64 FMA per clock x 2
+# flops x 2.07 GHz. (A run of independent FMA chains on every SM measured 1.3 TFLOP/s in
+# binary64 and 77 TFLOP/s in binary32, i.e. 2 and ~124 FMA per clock per SM.)
+FP64_FMA_TFLOPS = 1.26
+
+
 def workload_name(scale: int) -> str:
     """The benchmarked workload, named the same way by both arms."""
     return ("SpMV + SpMM(L=128) on R-MAT 2^%d (a=.57,b=.19,c=.19, 16 samples/row, dedup), binary32, nnz split "
@@ -404,6 +410,12 @@ def run_gpu(args):
                     res[kern] = {"ms": round(ms, 4), "nnz_per_s": nnz / (ms * 1e-3),
                                  "algorithmic_GBps": round(nbytes / (ms * 1e-3) / 1e9, 1),
                                  "hbm_frac": round(nbytes / (ms * 1e-3) / 1e9 / hbm, 4)}
+                    if name == "f64" and kern == "spmm":
+                        # binary64 SpMM is bound by the FP64 FMA rate, not by memory
+                        tf = 2.0 * L_COLS * nnz / (ms * 1e-3) / 1e12
+                        res[kern]["alu_roofline"] = {"bound": "alu", "achieved": round(tf, 3),
+                                                     "peak": FP64_FMA_TFLOPS, "unit": "TFLOP/s",
+                                                     "frac": round(tf / FP64_FMA_TFLOPS, 4)}
                 yh = yv.double().cpu().numpy()
                 Yh = np.zeros((n, L_COLS))
                 Yh[sel] = Yv[torch.from_numpy(sel).to(dev)].double().cpu().numpy()
