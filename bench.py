@@ -51,7 +51,7 @@ def parse_args(argv=None):
     p.add_argument("--scale", type=int, default=22, help="log2 of the matrix size (22 = the measured workload)")
     p.add_argument("--no-variants", action="store_true", help="skip the per-variant table")
     p.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of CPU oracle work for cpu_baseline")
-    p.add_argument("--e2e-steps", type=int, default=10)
+    p.add_argument("--e2e-steps", type=int, default=20)
     p.add_argument("--fixed-tune", default="",
                    help="UNIT,BLOCK,INFLIGHT: skip the autotuner and run SpMM with this tuning (nnz split)")
     p.add_argument("--rows", default="all",
