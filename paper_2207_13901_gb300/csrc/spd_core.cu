@@ -77,8 +77,9 @@ spd_status read_tune(const spd_tune *t, Tuning *out) {
         out->row_pieces = t->row_pieces;
     }
     if (t->block_threads) {
-        if (t->block_threads < 64 || t->block_threads > 1024 || t->block_threads % 32)
-            return fail(SPD_ERR_ARG, "block_threads %d not a multiple of 32 in [64, 1024]", t->block_threads);
+        // the warp kernels are compiled for blocks of at most 256 threads
+        if (t->block_threads < 64 || t->block_threads > 256 || t->block_threads % 32)
+            return fail(SPD_ERR_ARG, "block_threads %d not a multiple of 32 in [64, 256]", t->block_threads);
         out->block_threads = t->block_threads;
     }
     if (t->inflight) {
