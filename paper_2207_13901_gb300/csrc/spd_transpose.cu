@@ -23,6 +23,7 @@ constexpr int kSortGroups = 16;                      // groups of 32 items per w
 constexpr int kSortTile = kSortThreads * kSortGroups;  // 4096 items per block
 constexpr int kDigits = 256;
 constexpr int kScanTile = kSortThreads * 16;          // items per block of the scan
+static_assert(kSortThreads == kDigits, "the scatter gives each thread one digit");
 
 // Exclusive prefix sum of x over the 256 threads of a block; *total gets the block sum.
 // s_warp: 8 ints of shared memory.
@@ -136,19 +137,28 @@ __global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(int64_t N, con
 }
 
 // Stable scatter of tile b: warp w owns the items [b*T + 512w, b*T + 512w + 512) in 16
-// groups of 32. An item's destination is the scanned count of its (digit, tile), plus
-// the items of that digit in earlier warps of the tile, plus those in earlier groups of
-// its warp, plus those in lower lanes of its group. vals_in == NULL means the identity
-// payload (the item's own index).
+// groups of 32. An item's rank among the tile's items of its digit is the count of that
+// digit in earlier warps of the tile, plus in earlier groups of its warp, plus in lower
+// lanes of its group. The items are first placed in shared memory in tile order sorted
+// by digit (a stable local sort), then written out so that consecutive threads write
+// consecutive destinations inside each digit's run: destination = the scanned count of
+// (digit, tile) + the rank. vals_in == NULL means the identity payload (the item's own
+// index).
 __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(
     int64_t N, const int32_t *__restrict__ keys_in, const int32_t *__restrict__ vals_in, int shift,
     const int32_t *__restrict__ offs, int64_t ntiles, int32_t *__restrict__ keys_out,
     int32_t *__restrict__ vals_out) {
     __shared__ int32_t cnt[kSortWarps][kDigits];
+    __shared__ int32_t s_local[kDigits];   // first tile-local slot of each digit
+    __shared__ int32_t s_global[kDigits];  // first destination of each digit's run of this tile
+    __shared__ int32_t s_warp[kSortWarps];
+    __shared__ int32_t s_key[kSortTile], s_val[kSortTile];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int d = lane; d < kDigits; d += 32) cnt[w][d] = 0;
     __syncwarp();
-    const int64_t base = (int64_t)blockIdx.x * kSortTile + (int64_t)w * (32 * kSortGroups);
+    const int64_t tile0 = (int64_t)blockIdx.x * kSortTile;
+    const int64_t base = tile0 + (int64_t)w * (32 * kSortGroups);
+    const int items = (int)(N - tile0 < kSortTile ? N - tile0 : kSortTile);
     int32_t key[kSortGroups], val[kSortGroups];
 #pragma unroll
     for (int g = 0; g < kSortGroups; ++g) {
@@ -162,9 +172,17 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(
         __syncwarp();
     }
     __syncthreads();
-    // counts -> starting offsets: tile offset of the digit plus the earlier warps' counts
-    for (int d = threadIdx.x; d < kDigits; d += kSortThreads) {
-        int32_t run = offs[(int64_t)d * ntiles + blockIdx.x];
+    // per digit (one thread each): the tile's total, then each warp's first local slot
+    {
+        const int d = threadIdx.x;  // kSortThreads == kDigits
+        int32_t tot = 0;
+#pragma unroll
+        for (int ww = 0; ww < kSortWarps; ++ww) tot += cnt[ww][d];
+        int32_t all;
+        const int32_t start = block_exclusive_sum(tot, s_warp, &all);
+        s_local[d] = start;
+        s_global[d] = offs[(int64_t)d * ntiles + blockIdx.x];
+        int32_t run = start;
 #pragma unroll
         for (int ww = 0; ww < kSortWarps; ++ww) {
             const int32_t c = cnt[ww][d];
@@ -181,13 +199,21 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(
         const int d = valid ? (int)(((uint32_t)key[g] >> shift) & (kDigits - 1)) : kDigits;
         const unsigned peers = __match_any_sync(kFull, d);
         if (valid) {
-            const int32_t dest = cnt[w][d] + __popc(peers & below);
-            keys_out[dest] = key[g];
-            vals_out[dest] = val[g];
+            const int32_t slot = cnt[w][d] + __popc(peers & below);
+            s_key[slot] = key[g];
+            s_val[slot] = val[g];
         }
         __syncwarp();
         if (valid && lane == __ffs(peers) - 1) cnt[w][d] += __popc(peers);
         __syncwarp();
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < items; t += kSortThreads) {
+        const int32_t k = s_key[t];
+        const int d = (int)(((uint32_t)k >> shift) & (kDigits - 1));
+        const int32_t dest = s_global[d] + (t - s_local[d]);
+        keys_out[dest] = k;
+        vals_out[dest] = s_val[t];
     }
 }
 
