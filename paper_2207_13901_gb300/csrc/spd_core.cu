@@ -96,7 +96,7 @@ int resolve_split(int split) {
     return split;
 }
 
-WsLayout make_layout(int64_t npieces, int64_t width, bool need_partition, bool need_carry, bool aux) {
+WsLayout make_layout(int64_t npieces, int64_t width, bool need_partition, bool need_carry, bool aux, bool chunks) {
     WsLayout L;
     L.npieces = npieces;
     size_t off = 0;
@@ -115,6 +115,13 @@ WsLayout make_layout(int64_t npieces, int64_t width, bool need_partition, bool n
         off += align_up(sizeof(int32_t) * (size_t)npieces);
         L.carry_val = off;
         off += align_up(sizeof(double) * (size_t)npieces * (size_t)(width > 0 ? width : 1));
+        if (chunks) {
+            const int64_t nch = ceil_div(npieces, kCarryChunk);
+            L.chunk_row = off;
+            off += align_up(sizeof(int32_t) * (size_t)nch);
+            L.chunk_val = off;
+            off += align_up(sizeof(double) * (size_t)nch * (size_t)(width > 0 ? width : 1));
+        }
     }
     L.total = off;
     return L;
@@ -177,12 +184,12 @@ WsLayout layout_spmv(int64_t n, int64_t nnz, int split) {
 
 WsLayout layout_warp(int64_t n, int64_t nnz, int split, int64_t unit, int64_t width, bool carries) {
     if (split == SPD_SPLIT_ROW || n + nnz == 0) return make_layout(0, 0, false, false, false);
-    return make_layout(ceil_div(n + nnz, unit), width, true, carries, false);
+    return make_layout(ceil_div(n + nnz, unit), width, true, carries, false, carries);
 }
 
 WsLayout layout_mttkrp(int64_t F, int64_t nnz, int split, int64_t unit, int64_t R) {
     if (split == SPD_SPLIT_ROW || F + nnz == 0) return make_layout(0, 0, false, false, false);
-    return make_layout(ceil_div(F + nnz, unit), R, true, true, true);
+    return make_layout(ceil_div(F + nnz, unit), R, true, true, true, true);
 }
 
 // ------------------------------------------------------------------ partition kernels

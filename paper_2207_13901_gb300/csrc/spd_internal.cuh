@@ -345,10 +345,15 @@ int resolve_split(int split);
 struct WsLayout {
     int64_t npieces = 0;
     size_t part_row = 0, part_pos = 0, part_aux = 0, carry_row = 0, carry_val = 0;
+    size_t chunk_row = 0, chunk_val = 0;  // sums of the carries of kCarryChunk pieces
     size_t total = 0;
 };
-// npieces pieces, `width` carried values per piece, `aux` = extra int32 per boundary.
-WsLayout make_layout(int64_t npieces, int64_t width, bool need_partition, bool need_carry, bool aux);
+// Pieces per chunk of the two-level carry fix-up.
+constexpr int kCarryChunk = 32;
+// npieces pieces, `width` carried values per piece, `aux` = extra int32 per boundary,
+// `chunks` = room for the chunk sums of the row fix-up.
+WsLayout make_layout(int64_t npieces, int64_t width, bool need_partition, bool need_carry, bool aux,
+                     bool chunks = false);
 
 // Launches the fused non-zero partition of a level (pos, n parents, nnz children) into
 // the boundary arrays prow/ppos (npieces + 1 entries each).
@@ -405,12 +410,50 @@ inline spd_status launch_zero_rows(int64_t rows, int64_t L, OT *A, int64_t lda, 
 // Adds the binary64 carries of consecutive pieces that ended inside the same outer entry
 // (row or slice) to the value the completing piece wrote. One warp per piece, one lane
 // per column; only the first piece of each run does the work.
+// First level of the row fix-up: for every chunk of kCarryChunk consecutive pieces that
+// all ended inside the same row, the sum of their carries (in piece order) and that row;
+// other chunks get row -1. One warp per chunk, each lane EPL columns.
+template <int EPL>
+__global__ void carry_chunk_kernel(int64_t npieces, int64_t L, const int32_t *__restrict__ carry_row,
+                                   const double *__restrict__ carry_val, int32_t *__restrict__ chunk_row,
+                                   double *__restrict__ chunk_val) {
+    const int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    const int64_t nch = (npieces + kCarryChunk - 1) / kCarryChunk;
+    if (k >= nch) return;  // whole warp
+    const int64_t c0 = k * kCarryChunk;
+    const int32_t mine = c0 + lane < npieces ? carry_row[c0 + lane] : -2;
+    const int32_t row = __shfl_sync(0xffffffffu, mine, 0);
+    const bool whole = row >= 0 && __all_sync(0xffffffffu, mine == row);
+    if (blockIdx.y == 0 && lane == 0) chunk_row[k] = whole ? row : -1;
+    const int64_t col = ((int64_t)blockIdx.y * 32 + lane) * EPL;
+    if (!whole || col >= L) return;
+    double s[EPL];
+#pragma unroll
+    for (int e = 0; e < EPL; ++e) s[e] = 0.0;
+#pragma unroll 4
+    for (int d = 0; d < kCarryChunk; ++d) {
+        double v[EPL];
+        ld_vec<EPL>(carry_val + (c0 + d) * L + col, v);
+#pragma unroll
+        for (int e = 0; e < EPL; ++e) s[e] += v[e];
+    }
+    double *o = chunk_val + k * L + col;
+#pragma unroll
+    for (int e = 0; e < EPL; ++e) o[e] = s[e];
+}
+
 // Adds the binary64 carries of consecutive pieces that ended inside the same row to the
 // row the completing piece wrote: one warp per piece (only the first piece of a run
-// works), each lane EPL consecutive columns (vector loads of the carries and of Y).
+// works), each lane EPL consecutive columns (vector loads of the carries and of Y). A run
+// is walked piece by piece up to a chunk boundary, then a chunk at a time while whole
+// chunks lie inside it, then piece by piece again: a row spanning thousands of pieces
+// costs about a hundred dependent loads instead of thousands. The order of the sums is
+// fixed by the chunking, so results do not change from run to run.
 template <typename OT, int EPL>
 __global__ void carry_fixup_rows_kernel(int64_t npieces, int64_t L, const int32_t *__restrict__ carry_row,
-                                        const double *__restrict__ carry_val, OT *__restrict__ Y, int64_t ldy) {
+                                        const double *__restrict__ carry_val, const int32_t *__restrict__ chunk_row,
+                                        const double *__restrict__ chunk_val, OT *__restrict__ Y, int64_t ldy) {
     const int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int64_t col = ((int64_t)blockIdx.y * 32 + (threadIdx.x & 31)) * EPL;
     if (c >= npieces || col >= L) return;
@@ -419,38 +462,22 @@ __global__ void carry_fixup_rows_kernel(int64_t npieces, int64_t L, const int32_
     if (c > 0 && carry_row[c - 1] == row) return;
     double s[EPL];
     ld_vec<EPL>(carry_val + c * L + col, s);
-    if (c + 1 < npieces && carry_row[c + 1] == row) {
-        // a row spanning many pieces: its run is walked 8 pieces at a time, the 8 row tags
-        // loaded together and then the carries 4 at a time (about 36 round trips for
-        // ~100 pieces instead of ~100); the sum still runs in piece order
-        for (int64_t d = c + 1; d < npieces; d += 8) {
-            int32_t tag[8];
+    int64_t d = c + 1;
+    while (d < npieces) {
+        if (d % kCarryChunk == 0 && chunk_row[d / kCarryChunk] == row) {
+            double v[EPL];
+            ld_vec<EPL>(chunk_val + (d / kCarryChunk) * L + col, v);
 #pragma unroll
-            for (int k = 0; k < 8; ++k) tag[k] = d + k < npieces ? carry_row[d + k] : -1;
-            bool more = true;
-#pragma unroll 1
-            for (int h = 0; h < 8 && more; h += 4) {  // 4 carries in flight at a time
-                double v[4][EPL];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    if (tag[h + k] == row) {
-                        ld_vec<EPL>(carry_val + (d + h + k) * L + col, v[k]);
-                    } else {
-#pragma unroll
-                        for (int e = 0; e < EPL; ++e) v[k][e] = 0.0;
-                    }
-                }
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    more = more && tag[h + k] == row;
-                    if (more) {
-#pragma unroll
-                        for (int e = 0; e < EPL; ++e) s[e] += v[k][e];
-                    }
-                }
-            }
-            if (!more) break;
+            for (int e = 0; e < EPL; ++e) s[e] += v[e];
+            d += kCarryChunk;
+            continue;
         }
+        if (carry_row[d] != row) break;
+        double v[EPL];
+        ld_vec<EPL>(carry_val + d * L + col, v);
+#pragma unroll
+        for (int e = 0; e < EPL; ++e) s[e] += v[e];
+        ++d;
     }
     OT *yp = Y + (int64_t)row * ldy + col;
     OT o[EPL];
@@ -460,17 +487,24 @@ __global__ void carry_fixup_rows_kernel(int64_t npieces, int64_t L, const int32_
     st_vec(yp, o);
 }
 
+// Both levels of the row fix-up; chunk_row / chunk_val: the workspace's chunk area.
 template <typename OT>
-inline spd_status launch_carry_fixup(int64_t npieces, int64_t L, const int32_t *crow, const double *cval, OT *Y,
-                                     int64_t ldy, cudaStream_t st) {
+inline spd_status launch_carry_fixup(int64_t npieces, int64_t L, const int32_t *crow, const double *cval,
+                                     int32_t *chunk_row, double *chunk_val, OT *Y, int64_t ldy, cudaStream_t st) {
     if (npieces <= 0 || L <= 0) return SPD_OK;
-    const bool vec4 = L % 4 == 0 && ldy % 4 == 0 && aligned(Y, 4 * sizeof(OT)) && aligned(cval, 32);
+    const int64_t nch = (npieces + kCarryChunk - 1) / kCarryChunk;
+    const bool vec4 = L % 4 == 0 && ldy % 4 == 0 && aligned(Y, 4 * sizeof(OT)) && aligned(cval, 32) &&
+                      aligned(chunk_val, 32);
     if (vec4) {
+        carry_chunk_kernel<4><<<dim3((unsigned)ceil_div(nch, 8), (unsigned)ceil_div(L, 128)), 256, 0, st>>>(
+            npieces, L, crow, cval, chunk_row, chunk_val);
         dim3 grid((unsigned)ceil_div(npieces, 8), (unsigned)ceil_div(L, 128));
-        carry_fixup_rows_kernel<OT, 4><<<grid, 256, 0, st>>>(npieces, L, crow, cval, Y, ldy);
+        carry_fixup_rows_kernel<OT, 4><<<grid, 256, 0, st>>>(npieces, L, crow, cval, chunk_row, chunk_val, Y, ldy);
     } else {
+        carry_chunk_kernel<1><<<dim3((unsigned)ceil_div(nch, 8), (unsigned)ceil_div(L, 32)), 256, 0, st>>>(
+            npieces, L, crow, cval, chunk_row, chunk_val);
         dim3 grid((unsigned)ceil_div(npieces, 8), (unsigned)ceil_div(L, 32));
-        carry_fixup_rows_kernel<OT, 1><<<grid, 256, 0, st>>>(npieces, L, crow, cval, Y, ldy);
+        carry_fixup_rows_kernel<OT, 1><<<grid, 256, 0, st>>>(npieces, L, crow, cval, chunk_row, chunk_val, Y, ldy);
     }
     return check_launch("carry_fixup_rows_kernel");
 }

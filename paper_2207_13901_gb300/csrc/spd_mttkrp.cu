@@ -229,7 +229,8 @@ static spd_status launch_mttkrp_g(const spd_csf3 *B, const void *C, int64_t ldc,
         B->dim0, B->nfib, B->pos1, B->crd1, B->pos2, B->crd2, v, cc, ldc, dd, ldd, R, aa, lda, pfib, ppos, psl,
         Lw.npieces, 0, crow, cval);
     if ((s = check_launch("spmttkrp_warp_kernel(nnz)"))) return s;
-    return launch_carry_fixup<OT>(Lw.npieces, R, crow, cval, aa, lda, st);
+    return launch_carry_fixup<OT>(Lw.npieces, R, crow, cval, reinterpret_cast<int32_t *>(w + Lw.chunk_row),
+                                  reinterpret_cast<double *>(w + Lw.chunk_val), aa, lda, st);
 }
 
 template <typename VT, int EPL>

@@ -144,7 +144,8 @@ static spd_status launch_spmm_shape(const spd_csr *A, const void *X, int64_t L, 
         A->nrows, A->pos, A->crd, v, x, (uint32_t)(ldx * sizeof(VT)), y, ldy, L, prow, ppos, Lw.npieces, 0, crow,
         cval);
     if ((s = check_launch("spmm_warp_kernel(nnz)"))) return s;
-    return launch_carry_fixup<OT>(Lw.npieces, L, crow, cval, y, ldy, st);
+    return launch_carry_fixup<OT>(Lw.npieces, L, crow, cval, reinterpret_cast<int32_t *>(w + Lw.chunk_row),
+                                  reinterpret_cast<double *>(w + Lw.chunk_val), y, ldy, st);
 }
 
 // Rows in flight per group: the tuning's 4 or 8 for one entry per warp step in the
