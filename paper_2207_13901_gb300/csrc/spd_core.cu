@@ -206,14 +206,15 @@ __global__ void merge_partition_kernel(int64_t n, int64_t nnz, const int32_t *__
         ppos[npieces] = (int32_t)nnz;
         return;
     }
-    int64_t e = (int64_t)__ldg(pos + r + 1) + r;
+    // item indices stay below nrows + nnz < 2^32, so the divisions run in 32 bits
+    const uint32_t u = (uint32_t)unit;
+    const uint32_t e = (uint32_t)__ldg(pos + r + 1) + (uint32_t)r;
     int64_t t_lo = 0;
     if (r > 0) {
-        int64_t e_prev = (int64_t)__ldg(pos + r) + r - 1;
-        t_lo = e_prev / unit + 1;
+        const uint32_t e_prev = (uint32_t)__ldg(pos + r) + (uint32_t)r - 1u;
+        t_lo = (int64_t)(e_prev / u) + 1;
     }
-    int64_t t_hi = e / unit;
-    if (t_lo < 0) t_lo = 0;  // only reachable with a pos that breaks the format
+    int64_t t_hi = (int64_t)(e / u);
     if (t_hi > npieces - 1) t_hi = npieces - 1;
     for (int64_t t = t_lo; t <= t_hi; ++t) {
         prow[t] = (int32_t)r;
