@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(256) spmttkrp_warp_kernel(
     using AT = typename Traits<VT>::acc;
     using OT = typename Traits<VT>::out;
     constexpr int NPG = 32 / G;         // entries per warp step
-    constexpr int U = G == 32 ? 4 : 2;  // warp steps in flight
+    constexpr int U = 4;  // warp steps in flight
     __shared__ int32_t s_j_all[8][32], s_k_all[8][32], s_sl_all[8][32];
     __shared__ AT s_v_all[8][32];
     const int lane = threadIdx.x & 31;

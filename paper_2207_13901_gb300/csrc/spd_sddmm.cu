@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(256) sddmm_warp_kernel(
     using AT = typename Traits<VT>::acc;
     using OT = typename Traits<VT>::out;
     constexpr int NPG = 32 / G;                             // positions per warp step
-    constexpr int U = G == 32 ? 4 : 2;                      // warp steps in flight
+    constexpr int U = 4;                                    // warp steps in flight
     __shared__ int32_t s_crd_all[8][32], s_row_all[8][32];  // one window per warp (<= 8 warps)
     __shared__ AT s_val_all[8][32];
     const int lane = threadIdx.x & 31;
