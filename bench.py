@@ -334,8 +334,10 @@ def run_gpu(args):
     units, secs = aggregate(units_local, elapsed)
     value = units / secs
     ms_per_step = secs * 1e3 / args.steps
-    per_call = {"nnz": 3, "row": 1}  # partition + kernel + fix-up, or one kernel
-    launches = args.steps * (per_call[sp_v] + per_call[sp_m])
+    # nnz split: SpMV = partition + tile kernel + fix-up; SpMM = partition + warp kernel +
+    # chunk sums + row fix-up. Row split: one kernel each.
+    per_call = {("spmv", "nnz"): 3, ("spmm", "nnz"): 4, ("spmv", "row"): 1, ("spmm", "row"): 1}
+    launches = args.steps * (per_call[("spmv", sp_v)] + per_call[("spmm", sp_m)])
 
     hbm, peak_kind = measured_peaks()
     spmm_bytes = algorithmic_bytes("spmm", n, nnz, 4, 4, 4)
