@@ -144,9 +144,9 @@ def spmm_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(tune):
+def recorded_traffic(tune, scale):
     """DRAM bytes per SpMM call from the committed ncu summary, if it was taken on the
-    current kernel sources with the same tuning; otherwise None."""
+    same R-MAT scale, the current kernel sources and the same tuning; otherwise None."""
     if not os.path.exists(TRAFFIC_FILE):
         return None
     vals = {}
@@ -156,7 +156,7 @@ def recorded_traffic(tune):
                 k, v = line.strip()[2:].split(":", 1)
                 vals[k.strip()] = v.strip().strip("`")
     try:
-        if vals.get("source_hash") != spmm_source_hash():
+        if int(vals["scale"]) != scale or vals.get("source_hash") != spmm_source_hash():
             return None
         if vals.get("tune") != "%d,%d,%d" % (tune["unit_items"], tune["block_threads"], tune.get("inflight", 8)):
             return None
@@ -543,7 +543,7 @@ def run_gpu(args):
                 "peak_kind": peak_kind,
                 "unit": "GB/s",
                 "frac": round(spmm_gbs / hbm, 4),
-                "traffic": recorded_traffic(tu_m) if (sp_m == "nnz" and tu_m) else None,
+                "traffic": recorded_traffic(tu_m, args.scale) if (sp_m == "nnz" and tu_m) else None,
                 "traffic_source": "profiles/traffic_spmm_rmat22_f32.md (ncu dram__bytes_read.sum + dram__bytes_write.sum "
                                   "of the partition, warp and fix-up kernels of one call)",
                 "algorithmic_bytes": spmm_bytes,
