@@ -42,7 +42,8 @@
  *   - Argument errors are detected on the host before anything is launched and are
  *     returned as an spd_status; nothing is written in that case. Structure errors
  *     (a pos/crd that breaks the format) are NOT checked by the compute calls: run
- *     spd_csr_validate / spd_csf3_validate once per structure.
+ *     spd_csr_validate / spd_csf3_validate once per structure, or turn on checked
+ *     mode (spd_set_checked) while debugging.
  *   - Dense matrices are row-major with an explicit leading dimension (in elements).
  *   - Element types: values and dense inputs share one type t; results are binary64
  *     when t is SPD_F64 and binary32 otherwise. SPD_F32/SPD_BF16 accumulate in
@@ -69,7 +70,7 @@ typedef enum {
     SPD_ERR_SHAPE = 2,     /* a size is negative or sizes are inconsistent */
     SPD_ERR_DTYPE = 3,     /* unsupported element type or type combination */
     SPD_ERR_ALIGN = 4,     /* a pointer or leading dimension is misaligned */
-    SPD_ERR_STRUCTURE = 5, /* validate: the pos/crd arrays break the level format */
+    SPD_ERR_STRUCTURE = 5, /* validate or checked mode: pos/crd break the level format */
     SPD_ERR_WORKSPACE = 6, /* workspace NULL or smaller than the size query returned */
     SPD_ERR_CUDA = 7,      /* a CUDA runtime call or kernel launch failed */
     SPD_ERR_OOM = 8,       /* reserved: the compute calls allocate nothing */
@@ -150,6 +151,23 @@ const char *spd_status_str(int status);
 /* Detail of the last error returned on the calling thread (static buffer of the
  * thread; empty string when there is none). */
 const char *spd_last_error(void);
+
+/* Checked mode, for debugging (off by default; on from the start when the environment
+ * variable SPD_DEBUG is set to anything but "" or "0"). While it is on, every call that
+ * takes a sparse operand (partition, compute, transpose, column blocks, SpAdd3, batched
+ * plan) first validates that operand as spd_csr_validate / spd_csf3_validate do, through
+ * a status word in device memory, and returns SPD_ERR_STRUCTURE, with the operand's name
+ * and first bad index in spd_last_error(), before it launches any work on a broken one.
+ * Each call then synchronizes its stream, so that an execution error is returned by the
+ * call that caused it (SPD_ERR_CUDA). Checked calls therefore cannot be captured into a
+ * CUDA graph: the validation returns SPD_ERR_ARG during a capture (spd_spmm_batched_run,
+ * which validates nothing, is still captured; it skips the synchronization then). The
+ * validations of concurrent host threads are serialized. `on` is 0 or 1, else
+ * SPD_ERR_ARG. Process-wide; not meant to change while calls are in flight. */
+spd_status spd_set_checked(int on);
+
+/* 1 while checked mode is on, else 0. */
+int spd_checked(void);
 
 /* -------------------------------------------------------------------- sizes */
 

@@ -82,6 +82,8 @@ SIGNATURES = {
     "spd_abi_version": (ctypes.c_int, []),
     "spd_status_str": (ctypes.c_char_p, [_I]),
     "spd_last_error": (ctypes.c_char_p, []),
+    "spd_set_checked": (_I, [_I]),
+    "spd_checked": (ctypes.c_int, []),
     "spd_csr_workspace_size": (_I, [_I, _CSR, _I, _I64, _TUNE, ctypes.POINTER(ctypes.c_size_t)]),
     "spd_csf3_workspace_size": (_I, [_I, _CSF, _I, _I64, _TUNE, ctypes.POINTER(ctypes.c_size_t)]),
     "spd_csr_validate": (_I, [_CSR, _P, _SZ, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64), _P]),

@@ -241,6 +241,8 @@ spd_status spd_spmm_batched_plan(int64_t count, const spd_batch_item *items, int
     if (ws_bytes < B.total) return fail(SPD_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", ws_bytes, B.total);
     if (!aligned(ws, 256)) return fail(SPD_ERR_ALIGN, "workspace not 256-byte aligned");
     cudaStream_t st = as_stream(stream);
+    for (int64_t m = 0; m < count && checked_mode(); ++m)
+        if ((s = checked_csr(&items[m].A, "a batch matrix", st))) return s;
 
     // one lane shape that suits every matrix: lane groups only when every matrix allows
     // 16-byte vectors (decided by the largest X when the tuning leaves it open)
@@ -358,12 +360,14 @@ spd_status spd_spmm_batched_run(const spd_batch_plan *plan, void *stream) {
     if (plan->total_pieces == 0 || plan->L == 0) return SPD_OK;
     if (!plan->ws) return fail(SPD_ERR_WORKSPACE, "plan has no workspace");
     cudaStream_t st = as_stream(stream);
+    spd_status s;
     switch (plan->vtype) {
-        case SPD_F64: return dispatch_batched<double>(plan, st);
-        case SPD_F32: return dispatch_batched<float>(plan, st);
-        case SPD_BF16: return dispatch_batched<__nv_bfloat16>(plan, st);
+        case SPD_F64: s = dispatch_batched<double>(plan, st); break;
+        case SPD_F32: s = dispatch_batched<float>(plan, st); break;
+        case SPD_BF16: s = dispatch_batched<__nv_bfloat16>(plan, st); break;
         default: return fail(SPD_ERR_DTYPE, "unknown value type %d", plan->vtype);
     }
+    return checked_finish(s, "spd_spmm_batched_run", st);
 }
 
 }  // extern "C"

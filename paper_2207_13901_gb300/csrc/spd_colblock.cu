@@ -134,6 +134,7 @@ spd_status spd_csr_column_blocks(const spd_csr *A, int64_t nblk, const int32_t *
     if (ws_bytes < L.total) return fail(SPD_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", ws_bytes, L.total);
     if (!aligned(ws, 256)) return fail(SPD_ERR_ALIGN, "workspace not 256-byte aligned");
     cudaStream_t st = as_stream(stream);
+    if ((s = checked_csr(A, "A", st))) return s;
     char *w = static_cast<char *>(ws);
     int32_t *d_bounds = reinterpret_cast<int32_t *>(w + L.bounds);
     int32_t *d_totals = reinterpret_cast<int32_t *>(w + L.totals);

@@ -1,6 +1,10 @@
 // spd_core.cu -- status handling, argument checks, workspace layouts, the work
 // partitions (Sections II-B, III-A, IV-B/C) and structure validation (Section III-B).
+#include <atomic>
 #include <cstdarg>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
 
 #include "spd_internal.cuh"
 
@@ -310,6 +314,77 @@ static spd_status run_validate(int nlevels, const int64_t *nparent, const int64_
     return SPD_OK;
 }
 
+// ------------------------------------------------------------------ checked mode
+
+// -1 until the first query reads SPD_DEBUG from the environment; then 0 or 1.
+static std::atomic<int> g_checked{-1};
+// The device status word of checked mode (a ValidateOut, padded to the 64 bytes that
+// run_validate asks of a workspace); one per process, its users serialized by the mutex.
+static __device__ __align__(16) unsigned char g_checked_word[64];
+static std::mutex g_checked_mutex;
+
+bool checked_mode() {
+    int c = g_checked.load();
+    if (c < 0) {
+        const char *e = getenv("SPD_DEBUG");
+        c = (e && *e && strcmp(e, "0") != 0) ? 1 : 0;
+        int expected = -1;
+        if (!g_checked.compare_exchange_strong(expected, c)) c = expected;
+    }
+    return c == 1;
+}
+
+static spd_status not_capturing(cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess) return fail(SPD_ERR_CUDA, "checked mode: %s", cudaGetErrorString(e));
+    if (cs != cudaStreamCaptureStatusNone)
+        return fail(SPD_ERR_ARG, "checked mode synchronizes the stream and cannot run inside a graph capture");
+    return SPD_OK;
+}
+
+static spd_status checked_levels(int nlevels, const int64_t *np, const int64_t *dm, const int64_t *nc,
+                                 const int32_t *const *ps, const int32_t *const *cs, const char *name,
+                                 cudaStream_t st) {
+    spd_status s = not_capturing(st);
+    if (s) return s;
+    std::lock_guard<std::mutex> lock(g_checked_mutex);
+    void *word = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&word, g_checked_word);
+    if (e != cudaSuccess) return fail(SPD_ERR_CUDA, "checked mode: %s", cudaGetErrorString(e));
+    int64_t violations = 0, first_bad = -1;
+    s = run_validate(nlevels, np, dm, nc, ps, cs, word, sizeof(g_checked_word), &violations, &first_bad, st);
+    if (s == SPD_ERR_STRUCTURE)
+        return fail(s, "checked mode: %s breaks the level format (%lld violations, first at index %lld)", name,
+                    (long long)violations, (long long)first_bad);
+    return s;
+}
+
+spd_status checked_csr(const spd_csr *A, const char *name, cudaStream_t st) {
+    if (!checked_mode()) return SPD_OK;
+    int64_t np[1] = {A->nrows}, dm[1] = {A->ncols}, nc[1] = {A->nnz};
+    const int32_t *ps[1] = {A->pos}, *cs[1] = {A->crd};
+    return checked_levels(1, np, dm, nc, ps, cs, name, st);
+}
+
+spd_status checked_csf3(const spd_csf3 *B, const char *name, cudaStream_t st) {
+    if (!checked_mode()) return SPD_OK;
+    int64_t np[2] = {B->dim0, B->nfib}, dm[2] = {B->dim1, B->dim2}, nc[2] = {B->nfib, B->nnz};
+    const int32_t *ps[2] = {B->pos1, B->pos2}, *cs[2] = {B->crd1, B->crd2};
+    return checked_levels(2, np, dm, nc, ps, cs, name, st);
+}
+
+spd_status checked_finish(spd_status s, const char *call, cudaStream_t st) {
+    if (s != SPD_OK || !checked_mode()) return s;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cs);
+    if (e == cudaSuccess && cs != cudaStreamCaptureStatusNone) return SPD_OK;  // captured work runs later
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(SPD_ERR_CUDA, "%s: %s", call, cudaGetErrorString(e));
+    return SPD_OK;
+}
+
 }  // namespace spd
 
 using namespace spd;
@@ -336,6 +411,14 @@ const char *spd_status_str(int s) {
 }
 
 const char *spd_last_error(void) { return g_last_error; }
+
+spd_status spd_set_checked(int on) {
+    if (on != 0 && on != 1) return fail(SPD_ERR_ARG, "spd_set_checked takes 0 or 1, not %d", on);
+    g_checked.store(on);
+    return SPD_OK;
+}
+
+int spd_checked(void) { return checked_mode() ? 1 : 0; }
 
 spd_status spd_csr_validate(const spd_csr *A, void *ws, size_t ws_bytes, int64_t *violations, int64_t *first_bad,
                             void *stream) {
@@ -411,9 +494,10 @@ spd_status spd_csr_partition(const spd_csr *A, int split, int64_t npieces, int64
     split = resolve_split(split);
     if (split == SPD_SPLIT_ROW) {
         if (npieces < 1 || npieces > INT32_MAX) return fail(SPD_ERR_ARG, "npieces %lld out of range", (long long)npieces);
+        if ((s = checked_csr(A, "A", st))) return s;
         int64_t grid = ceil_div(npieces + 1, 256);
         row_partition_kernel<<<(unsigned)grid, 256, 0, st>>>(A->nrows, A->pos, npieces, rows_out, pos_out);
-        return check_launch("row_partition_kernel");
+        return checked_finish(check_launch("row_partition_kernel"), "spd_csr_partition", st);
     }
     if (split != SPD_SPLIT_NNZ) return fail(SPD_ERR_ARG, "unknown split %d", split);
     if (unit_items < 1) return fail(SPD_ERR_ARG, "unit_items %lld < 1", (long long)unit_items);
@@ -421,7 +505,9 @@ spd_status spd_csr_partition(const spd_csr *A, int split, int64_t npieces, int64
     if (npieces != want)
         return fail(SPD_ERR_SHAPE, "npieces %lld != ceil((nrows+nnz)/unit_items) = %lld", (long long)npieces,
                     (long long)want);
-    return launch_merge_partition(A->nrows, A->nnz, A->pos, unit_items, npieces, rows_out, pos_out, st);
+    if ((s = checked_csr(A, "A", st))) return s;
+    return checked_finish(launch_merge_partition(A->nrows, A->nnz, A->pos, unit_items, npieces, rows_out, pos_out, st),
+                          "spd_csr_partition", st);
 }
 
 }  // extern "C"

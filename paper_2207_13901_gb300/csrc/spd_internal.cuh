@@ -323,6 +323,16 @@ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 spd_status check_csr(const spd_csr *A, bool need_vals);
 spd_status check_csf3(const spd_csf3 *B);
 
+// Checked mode (spd_set_checked / SPD_DEBUG=1 in the environment). When it is on, the
+// compute calls validate their sparse operands through a device status word before they
+// launch anything (returning SPD_ERR_STRUCTURE with the first bad index), and wait for
+// their own work afterwards so that a launch or execution error is reported by the call
+// that caused it. Both helpers return SPD_OK at once when checked mode is off.
+bool checked_mode();
+spd_status checked_csr(const spd_csr *A, const char *name, cudaStream_t st);
+spd_status checked_csf3(const spd_csf3 *B, const char *name, cudaStream_t st);
+spd_status checked_finish(spd_status s, const char *call, cudaStream_t st);
+
 // Defaults shared by the size queries and the compute calls.
 constexpr int kSpmvThreads = 256;   // threads of the tile-per-block SpMV / SpTTV kernel
 constexpr int kSpmvIPT = 8;         // items per thread of one tile

@@ -276,12 +276,14 @@ extern "C" spd_status spd_spmttkrp(const spd_csf3 *B, const void *C, int64_t ldc
     if (split != SPD_SPLIT_ROW && split != SPD_SPLIT_NNZ) return fail(SPD_ERR_ARG, "unknown split %d", split);
     WsLayout Lw = layout_mttkrp(B->nfib, B->nnz, split, tn.unit_items, R);
     if ((s = check_ws(Lw, ws, ws_bytes))) return s;
-    if (B->dim0 == 0 || R == 0) return SPD_OK;
     cudaStream_t st = as_stream(stream);
+    if ((s = checked_csf3(B, "B", st))) return s;
+    if (B->dim0 == 0 || R == 0) return SPD_OK;
     switch (B->vtype) {
-        case SPD_F64: return launch_mttkrp<double>(B, C, ldc, D, ldd, R, A, lda, split, tn, ws, st);
-        case SPD_F32: return launch_mttkrp<float>(B, C, ldc, D, ldd, R, A, lda, split, tn, ws, st);
-        case SPD_BF16: return launch_mttkrp<__nv_bfloat16>(B, C, ldc, D, ldd, R, A, lda, split, tn, ws, st);
+        case SPD_F64: s = launch_mttkrp<double>(B, C, ldc, D, ldd, R, A, lda, split, tn, ws, st); break;
+        case SPD_F32: s = launch_mttkrp<float>(B, C, ldc, D, ldd, R, A, lda, split, tn, ws, st); break;
+        case SPD_BF16: s = launch_mttkrp<__nv_bfloat16>(B, C, ldc, D, ldd, R, A, lda, split, tn, ws, st); break;
         default: return fail(SPD_ERR_DTYPE, "unknown value type %d", B->vtype);
     }
+    return checked_finish(s, "spd_spmttkrp", st);
 }

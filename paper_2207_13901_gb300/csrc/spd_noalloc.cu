@@ -65,10 +65,12 @@ extern "C" spd_status spd_spmv_noalloc(const spd_csr *A, const void *x, int x_ty
                     "nrows + nnz = %lld needs %zu bytes of scratch; spd_spmv_noalloc has %zu (use spd_spmv with a "
                     "workspace)",
                     (long long)(A->nrows + A->nnz), L.total, kNoAllocScratchBytes);
+    cudaStream_t st = as_stream(stream);
+    if ((s = checked_csr(A, "A", st))) return s;
     if (A->nrows == 0) return SPD_OK;
     void *scratch = nullptr;
     if ((s = noalloc_scratch(&scratch))) return s;
     // Every scratch byte the kernels read is written earlier in the same call (partition
     // boundaries, then one carry per piece), so nothing has to be cleared between calls.
-    return spmv_nnz_on_scratch(A, x, y, scratch, as_stream(stream));
+    return checked_finish(spmv_nnz_on_scratch(A, x, y, scratch, st), "spd_spmv_noalloc", st);
 }

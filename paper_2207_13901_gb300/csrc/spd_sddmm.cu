@@ -169,12 +169,14 @@ extern "C" spd_status spd_sddmm(const spd_csr *B, const void *C, int64_t K, int6
     if (split != SPD_SPLIT_ROW && split != SPD_SPLIT_NNZ) return fail(SPD_ERR_ARG, "unknown split %d", split);
     WsLayout Lw = layout_warp(B->nrows, B->nnz, split, tn.unit_items, 0, false);
     if ((s = check_ws(Lw, ws, ws_bytes))) return s;
-    if (B->nnz == 0) return SPD_OK;
     cudaStream_t st = as_stream(stream);
+    if ((s = checked_csr(B, "B", st))) return s;
+    if (B->nnz == 0) return SPD_OK;
     switch (B->vtype) {
-        case SPD_F64: return launch_sddmm<double>(B, C, K, ldc, Dnk, ldd, out_vals, split, tn, ws, st);
-        case SPD_F32: return launch_sddmm<float>(B, C, K, ldc, Dnk, ldd, out_vals, split, tn, ws, st);
-        case SPD_BF16: return launch_sddmm<__nv_bfloat16>(B, C, K, ldc, Dnk, ldd, out_vals, split, tn, ws, st);
+        case SPD_F64: s = launch_sddmm<double>(B, C, K, ldc, Dnk, ldd, out_vals, split, tn, ws, st); break;
+        case SPD_F32: s = launch_sddmm<float>(B, C, K, ldc, Dnk, ldd, out_vals, split, tn, ws, st); break;
+        case SPD_BF16: s = launch_sddmm<__nv_bfloat16>(B, C, K, ldc, Dnk, ldd, out_vals, split, tn, ws, st); break;
         default: return fail(SPD_ERR_DTYPE, "unknown value type %d", B->vtype);
     }
+    return checked_finish(s, "spd_sddmm", st);
 }

@@ -256,6 +256,13 @@ static spd_status check_spadd3(const spd_csr *B, const spd_csr *C, const spd_csr
     return SPD_OK;
 }
 
+static spd_status checked_operands(const spd_csr *B, const spd_csr *C, const spd_csr *D, cudaStream_t st) {
+    spd_status s = checked_csr(B, "B", st);
+    if (!s) s = checked_csr(C, "C", st);
+    if (!s) s = checked_csr(D, "D", st);
+    return s;
+}
+
 static Csr3 make_csr3(const spd_csr *B, const spd_csr *C, const spd_csr *D) {
     Csr3 m;
     const spd_csr *a[3] = {B, C, D};
@@ -321,6 +328,7 @@ spd_status spd_spadd3_symbolic(const spd_csr *B, const spd_csr *C, const spd_csr
     if (ws_bytes < L.total) return fail(SPD_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", ws_bytes, L.total);
     if (!aligned(ws, 256)) return fail(SPD_ERR_ALIGN, "workspace not 256-byte aligned");
     cudaStream_t st = as_stream(stream);
+    if ((s = checked_operands(B, C, D, st))) return s;
     char *w = static_cast<char *>(ws);
     const Csr3 m = make_csr3(B, C, D);
     int32_t *psum = reinterpret_cast<int32_t *>(w + L.psum);
@@ -376,16 +384,18 @@ spd_status spd_spadd3_numeric(const spd_csr *B, const spd_csr *C, const spd_csr 
     if (!ws) return fail(SPD_ERR_WORKSPACE, "workspace is NULL (%zu bytes needed)", L.total);
     if (ws_bytes < L.total) return fail(SPD_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", ws_bytes, L.total);
     if (!aligned(ws, 256)) return fail(SPD_ERR_ALIGN, "workspace not 256-byte aligned");
-    if (L.npieces == 0 || a_nnz == 0) return SPD_OK;
     cudaStream_t st = as_stream(stream);
+    if ((s = checked_operands(B, C, D, st))) return s;
+    if (L.npieces == 0 || a_nnz == 0) return SPD_OK;
     const Csr3 m = make_csr3(B, C, D);
     char *w = static_cast<char *>(ws);
     const bool nnz_split = split == SPD_SPLIT_NNZ;
     switch (B->vtype) {
-        case SPD_F64: return launch_spadd3<double, true>(B, m, L, nnz_split, w, nullptr, a_crd, a_vals, st);
-        case SPD_F32: return launch_spadd3<float, true>(B, m, L, nnz_split, w, nullptr, a_crd, a_vals, st);
-        default: return launch_spadd3<__nv_bfloat16, true>(B, m, L, nnz_split, w, nullptr, a_crd, a_vals, st);
+        case SPD_F64: s = launch_spadd3<double, true>(B, m, L, nnz_split, w, nullptr, a_crd, a_vals, st); break;
+        case SPD_F32: s = launch_spadd3<float, true>(B, m, L, nnz_split, w, nullptr, a_crd, a_vals, st); break;
+        default: s = launch_spadd3<__nv_bfloat16, true>(B, m, L, nnz_split, w, nullptr, a_crd, a_vals, st);
     }
+    return checked_finish(s, "spd_spadd3_numeric", st);
 }
 
 }  // extern "C"

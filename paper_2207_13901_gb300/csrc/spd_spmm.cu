@@ -251,14 +251,16 @@ static spd_status spmm_entry(const spd_csr *A, const void *X, int64_t L, int64_t
     if (split != SPD_SPLIT_ROW && split != SPD_SPLIT_NNZ) return fail(SPD_ERR_ARG, "unknown split %d", split);
     WsLayout Lw = layout_warp(A->nrows, A->nnz, split, tn.unit_items, L, true);
     if ((s = check_ws(Lw, ws, ws_bytes))) return s;
-    if (A->nrows == 0 || L == 0) return SPD_OK;
     cudaStream_t st = as_stream(stream);
+    if ((s = checked_csr(A, "A", st))) return s;
+    if (A->nrows == 0 || L == 0) return SPD_OK;
     switch (A->vtype) {
-        case SPD_F64: return launch_spmm<double>(A, X, L, ldx, Y, ldy, split, tn, ws, st, accumulate);
-        case SPD_F32: return launch_spmm<float>(A, X, L, ldx, Y, ldy, split, tn, ws, st, accumulate);
-        case SPD_BF16: return launch_spmm<__nv_bfloat16>(A, X, L, ldx, Y, ldy, split, tn, ws, st, accumulate);
+        case SPD_F64: s = launch_spmm<double>(A, X, L, ldx, Y, ldy, split, tn, ws, st, accumulate); break;
+        case SPD_F32: s = launch_spmm<float>(A, X, L, ldx, Y, ldy, split, tn, ws, st, accumulate); break;
+        case SPD_BF16: s = launch_spmm<__nv_bfloat16>(A, X, L, ldx, Y, ldy, split, tn, ws, st, accumulate); break;
         default: return fail(SPD_ERR_DTYPE, "unknown value type %d", A->vtype);
     }
+    return checked_finish(s, accumulate ? "spd_spmm_accumulate" : "spd_spmm", st);
 }
 
 extern "C" {
@@ -290,14 +292,16 @@ spd_status spd_spmm_t(const spd_csr *A, const void *dY, int64_t L, int64_t ldy, 
     if (split != SPD_SPLIT_ROW && split != SPD_SPLIT_NNZ) return fail(SPD_ERR_ARG, "unknown split %d", split);
     WsLayout Lw = layout_warp(A->nrows, A->nnz, split, tn.unit_items, L, false);
     if ((s = check_ws(Lw, ws, ws_bytes))) return s;
-    if (L == 0) return SPD_OK;
     cudaStream_t st = as_stream(stream);
+    if ((s = checked_csr(A, "A", st))) return s;
+    if (L == 0) return SPD_OK;
     switch (A->vtype) {
-        case SPD_F64: return launch_spmm_t<double>(A, dY, L, ldy, dX, ldx, split, tn, ws, st);
-        case SPD_F32: return launch_spmm_t<float>(A, dY, L, ldy, dX, ldx, split, tn, ws, st);
-        case SPD_BF16: return launch_spmm_t<__nv_bfloat16>(A, dY, L, ldy, dX, ldx, split, tn, ws, st);
+        case SPD_F64: s = launch_spmm_t<double>(A, dY, L, ldy, dX, ldx, split, tn, ws, st); break;
+        case SPD_F32: s = launch_spmm_t<float>(A, dY, L, ldy, dX, ldx, split, tn, ws, st); break;
+        case SPD_BF16: s = launch_spmm_t<__nv_bfloat16>(A, dY, L, ldy, dX, ldx, split, tn, ws, st); break;
         default: return fail(SPD_ERR_DTYPE, "unknown value type %d", A->vtype);
     }
+    return checked_finish(s, "spd_spmm_t", st);
 }
 
 }  // extern "C"

@@ -319,9 +319,12 @@ spd_status spd_spmv(const spd_csr *A, const void *x, int x_type, void *y, int y_
     if (split != SPD_SPLIT_ROW && split != SPD_SPLIT_NNZ) return fail(SPD_ERR_ARG, "unknown split %d", split);
     WsLayout L = layout_spmv(A->nrows, A->nnz, split);
     if ((s = check_ws(L, ws, ws_bytes))) return s;
+    cudaStream_t st = as_stream(stream);
+    if ((s = checked_csr(A, "A", st))) return s;
     if (A->nrows == 0) return SPD_OK;
-    return dispatch_spmv(A->vtype, A->nrows, A->nnz, A->pos, A->crd, A->vals, x, y, split, tn, 0, nullptr, ws,
-                         as_stream(stream));
+    return checked_finish(
+        dispatch_spmv(A->vtype, A->nrows, A->nnz, A->pos, A->crd, A->vals, x, y, split, tn, 0, nullptr, ws, st),
+        "spd_spmv", st);
 }
 
 spd_status spd_spttv(const spd_csf3 *B, const void *c, int c_type, void *out_vals, int out_type, int split,
@@ -340,14 +343,17 @@ spd_status spd_spttv(const spd_csf3 *B, const void *c, int c_type, void *out_val
     if (split != SPD_SPLIT_ROW && split != SPD_SPLIT_NNZ) return fail(SPD_ERR_ARG, "unknown split %d", split);
     WsLayout L = layout_spmv(B->nfib, B->nnz, split);
     if ((s = check_ws(L, ws, ws_bytes))) return s;
+    cudaStream_t st = as_stream(stream);
+    if ((s = checked_csf3(B, "B", st))) return s;
     if (B->nfib == 0) return SPD_OK;
     if (split == SPD_SPLIT_ROW && tn.row_pieces <= 0) {
         int64_t P = ceil_div(B->nfib + B->nnz, kSpmvTile);
         tn.row_pieces = P < B->dim0 ? P : B->dim0;
         if (tn.row_pieces < 1) tn.row_pieces = 1;
     }
-    return dispatch_spmv(B->vtype, B->nfib, B->nnz, B->pos2, B->crd2, B->vals, c, out_vals, split, tn, B->dim0,
-                         split == SPD_SPLIT_ROW ? B->pos1 : nullptr, ws, as_stream(stream));
+    return checked_finish(dispatch_spmv(B->vtype, B->nfib, B->nnz, B->pos2, B->crd2, B->vals, c, out_vals, split, tn,
+                                        B->dim0, split == SPD_SPLIT_ROW ? B->pos1 : nullptr, ws, st),
+                          "spd_spttv", st);
 }
 
 }  // extern "C"

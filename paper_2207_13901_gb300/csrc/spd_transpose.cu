@@ -328,6 +328,7 @@ spd_status spd_csr_transpose(const spd_csr *A, int32_t *t_pos, int32_t *t_crd, i
     if (ws_bytes < T.total) return fail(SPD_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", ws_bytes, T.total);
     if (!aligned(ws, 256)) return fail(SPD_ERR_ALIGN, "workspace not 256-byte aligned");
     cudaStream_t st = as_stream(stream);
+    if ((s = checked_csr(A, "A", st))) return s;
     char *w = static_cast<char *>(ws);
     int32_t *keys[2] = {reinterpret_cast<int32_t *>(w + T.keys0), reinterpret_cast<int32_t *>(w + T.keys1)};
     int32_t *pay = reinterpret_cast<int32_t *>(w + T.pay);
@@ -360,7 +361,7 @@ spd_status spd_csr_transpose(const spd_csr *A, int32_t *t_pos, int32_t *t_crd, i
         if ((s = check_launch("gather_rows_kernel"))) return s;
     }
     col_bounds_kernel<<<grid_for(N + 1, 256), 256, 0, st>>>(N, m, skeys, t_pos);
-    return check_launch("col_bounds_kernel");
+    return checked_finish(check_launch("col_bounds_kernel"), "spd_csr_transpose", st);
 }
 
 spd_status spd_gather_vals(int64_t n, const int32_t *perm, const void *in, void *out, int vtype, void *stream) {
@@ -385,7 +386,7 @@ spd_status spd_gather_vals(int64_t n, const int32_t *perm, const void *in, void 
             gather_vals_kernel<uint16_t><<<g, 256, 0, st>>>(n, perm, static_cast<const uint16_t *>(in),
                                                              static_cast<uint16_t *>(out));
     }
-    return check_launch("gather_vals_kernel");
+    return checked_finish(check_launch("gather_vals_kernel"), "spd_gather_vals", st);
 }
 
 }  // extern "C"

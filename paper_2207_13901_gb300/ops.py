@@ -247,6 +247,17 @@ def validate(T) -> Tuple[int, int]:
     return int(v.value), int(f.value)
 
 
+def set_checked(on: bool) -> None:
+    """Turns the library's checked mode on or off (``spd_set_checked``): every call that
+    takes a sparse operand validates it first and synchronizes its stream afterwards."""
+    _abi.check("spd_set_checked", _abi.load().spd_set_checked(1 if on else 0))
+
+
+def checked() -> bool:
+    """True while the library's checked mode is on (``spd_checked``)."""
+    return bool(_abi.load().spd_checked())
+
+
 def partition(A: CSR, split: str, npieces: int, unit_items: int = 0):
     """The work partition the kernels use, as two int32 device tensors of npieces + 1."""
     lib = _abi.load()

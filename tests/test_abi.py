@@ -3,6 +3,8 @@ that include/spd.h declares, and rejects bad arguments on the host before any la
 import ctypes
 import os
 import re
+import subprocess
+import sys
 
 import pytest
 
@@ -38,6 +40,29 @@ def test_status_strings_and_version():
     for s in range(11):
         assert lib.spd_status_str(s)
     assert lib.spd_status_str(99) == b"unknown status"
+
+
+def test_checked_mode_switch():
+    lib = _abi.load()
+    assert lib.spd_set_checked(2) == 10
+    assert lib.spd_set_checked(1) == 0 and lib.spd_checked() == 1
+    try:
+        # argument errors are still returned on the host first, before any validation
+        bad = _csr(nrows=-1)
+        assert lib.spd_spmv(ctypes.byref(bad), None, 1, None, 1, 1, None, None, 0, None) == 2
+    finally:
+        assert lib.spd_set_checked(0) == 0
+    assert lib.spd_checked() == 0
+
+
+def test_checked_mode_from_environment():
+    code = "from paper_2207_13901_gb300 import _abi; print(_abi.load().spd_checked())"
+    for value, want in (("1", "1"), ("yes", "1"), ("0", "0"), ("", "0")):
+        env = dict(os.environ, SPD_DEBUG=value)
+        out = subprocess.run([sys.executable, "-c", code], env=env, cwd=ROOT, capture_output=True, text=True,
+                             timeout=300)
+        assert out.returncode == 0, out.stderr
+        assert out.stdout.strip() == want
 
 
 def _csr(nrows=4, ncols=5, nnz=6, vtype=_abi.SPD_F32):
