@@ -113,6 +113,8 @@ def workload(scale: int):
 # flops x 2.07 GHz. (A run of independent FMA chains on every SM measured 1.3 TFLOP/s in
 # binary64 and 77 TFLOP/s in binary32, i.e. 2 and ~124 FMA per clock per SM.)
 FP64_FMA_TFLOPS = 1.26
+# GB300's nominal HBM3e bandwidth, reported beside the measured copy bandwidth
+HBM_NOMINAL_GBS = 7900.0
 
 
 def workload_name(scale: int) -> str:
@@ -328,8 +330,12 @@ def run_gpu(args):
     time.sleep(0.1)
     clocks.stop()
     elapsed = t0.elapsed_time(t1) / 1e3
-    spmv_ms = statistics.mean(m[0].elapsed_time(m[1]) for m in marks)
-    spmm_ms = statistics.mean(m[1].elapsed_time(m[2]) for m in marks)
+    spmv_calls = [m[0].elapsed_time(m[1]) for m in marks]
+    spmm_calls = [m[1].elapsed_time(m[2]) for m in marks]
+    spmv_ms = statistics.mean(spmv_calls)
+    spmm_ms = statistics.mean(spmm_calls)
+    call_ms = {k: {"mean": round(statistics.mean(v), 4), "median": round(statistics.median(v), 4),
+                   "min": round(min(v), 4)} for k, v in (("spmv", spmv_calls), ("spmm", spmm_calls))}
     units_local = 2.0 * nnz * args.steps
     units, secs = aggregate(units_local, elapsed)
     value = units / secs
@@ -487,9 +493,9 @@ def run_gpu(args):
     del bufs
 
     # ---------------- CPU oracle on a bounded row sample (rank 0, N = 1 only)
-    cpu = None
+    cpu = cpu_threaded = None
     if rank == 0 and ws == 1:
-        cpu = cpu_baseline(A, x32, X32, args.cpu_budget)
+        cpu, cpu_threaded = cpu_baseline(A, x32, X32, args.cpu_budget)
 
     rows_out = {}
     wanted = {"cfg1", "sddmm", "backward", "csf", "batched", "banded", "spadd3", "colblock"} if args.rows == "all" else \
@@ -511,6 +517,12 @@ def run_gpu(args):
             rows_out[name] = {"failed": "%s: %s" % (type(exc).__name__, exc)}
 
     clk = clocks.summary()
+    props = torch.cuda.get_device_properties(dev)
+    sm_count = props.multi_processor_count
+    l2_bytes = getattr(props, "L2_cache_size", None)
+    # binary32 CUDA-core ridge: 128 FMA lanes per SM, 2 flops each, at the sampled clock
+    ridge_mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz")
+    fp32_ridge = (2 * 128 * sm_count * ridge_mhz * 1e6 / (hbm * 1e9)) if ridge_mhz else None
     if rank == 0:
         line = {
             "metric": "nonzeros/s",
@@ -535,11 +547,18 @@ def run_gpu(args):
                 "generate_s": round(gen_s, 1),
             },
             "kernel_ms": {"spmv": round(spmv_ms, 4), "spmm": round(spmm_ms, 4)},
+            "call_ms": call_ms,
             "roofline": {
                 "bound": "hbm",
                 "kernel": "spd_spmm (partition + spmm_warp_kernel + carry fix-up), binary32, %s split" % sp_m,
                 "achieved": round(spmm_gbs, 1),
                 "peak": hbm,
+                "peak_nominal": HBM_NOMINAL_GBS,
+                "frac_nominal": round(spmm_gbs / HBM_NOMINAL_GBS, 4),
+                "intensity_flop_per_byte": round(2.0 * L_COLS * nnz / spmm_bytes, 3),
+                "fp32_ridge_flop_per_byte": round(fp32_ridge, 2) if fp32_ridge else None,
+                "sm_count": sm_count,
+                "l2_bytes": l2_bytes,
                 "peak_kind": peak_kind,
                 "unit": "GB/s",
                 "frac": round(spmm_gbs / hbm, 4),
@@ -556,6 +575,7 @@ def run_gpu(args):
             "gpu_launches": launches,
             "clocks": clk,
             "cpu_baseline": cpu,
+            "cpu_baseline_threaded": cpu_threaded,
             "variants": variants,
             "autotune": {"spmm": spmm_table, "spmv": spmv_table},
             "rows": rows_out,
@@ -999,7 +1019,34 @@ def cpu_calibrate(A, x, X):
     return (time.perf_counter() - t) / max(snnz, 1)
 
 
+def host_threads() -> int:
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except AttributeError:
+        return max(1, os.cpu_count() or 1)
+
+
+def oracle_rows_threaded(A, x, X, sel, threads):
+    """The oracle's SpMV and SpMM over the rows `sel`, dealt round-robin to `threads` host
+    threads (the oracle's C loops run without the interpreter lock; every row is summed
+    in the same order as in one thread, so the results are the same). Returns seconds."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    parts = [sel[t::threads] for t in range(threads)]
+
+    def work(rows):
+        oracle.spmv(A.pos, A.crd, A.vals, x, sel=rows)
+        oracle.spmm(A.pos, A.crd, A.vals, X, sel=rows)
+
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        t = time.perf_counter()
+        list(ex.map(work, parts))
+        return time.perf_counter() - t
+
+
 def cpu_baseline(A, x32, X32, budget):
+    """The oracle on a row sample: one thread (`cpu_baseline`) and, on the same rows, one
+    thread per host core (`threaded`)."""
     import oracle
     x = x32.astype(np.float64)
     X = X32.astype(np.float64)
@@ -1010,9 +1057,13 @@ def cpu_baseline(A, x32, X32, budget):
     oracle.spmv(A.pos, A.crd, A.vals, x, sel=sel)
     oracle.spmm(A.pos, A.crd, A.vals, X, sel=sel)
     dt = time.perf_counter() - t
-    return {"value": 2.0 * snnz / dt, "unit": "nnz/s", "cores": 1, "kind": "oracle",
-            "sample": "every %d-th row of the matrix (%d rows, %d nonzeros), SpMV + SpMM(L=128) in binary64, "
-                      "single thread, %.1f s" % (k, sel.size, snnz, dt)}
+    what = "every %d-th row of the matrix (%d rows, %d nonzeros), SpMV + SpMM(L=128) in binary64" % (k, sel.size, snnz)
+    T = host_threads()
+    dt_t = oracle_rows_threaded(A, x, X, sel, T)
+    return ({"value": 2.0 * snnz / dt, "unit": "nnz/s", "cores": 1, "kind": "oracle",
+             "sample": "%s, single thread, %.1f s" % (what, dt)},
+            {"value": 2.0 * snnz / dt_t, "unit": "nnz/s", "cores": T, "kind": "oracle",
+             "sample": "%s, rows dealt to %d host threads, %.1f s" % (what, T, dt_t)})
 
 
 def run_reference(args):
@@ -1028,25 +1079,23 @@ def run_reference(args):
     budget = 120.0 / max(1, args.steps + args.warmup)  # whole run within a few minutes
     sel, k = cpu_sample(A, budget, per)
     snnz = int(np.diff(A.pos)[sel].sum())
+    T = host_threads()
     for _ in range(args.warmup):
-        oracle.spmv(A.pos, A.crd, A.vals, x, sel=sel)
-        oracle.spmm(A.pos, A.crd, A.vals, X, sel=sel)
-    t = time.perf_counter()
+        oracle_rows_threaded(A, x, X, sel, T)
+    dt = 0.0
     for _ in range(args.steps):
-        oracle.spmv(A.pos, A.crd, A.vals, x, sel=sel)
-        oracle.spmm(A.pos, A.crd, A.vals, X, sel=sel)
-    dt = time.perf_counter() - t
+        dt += oracle_rows_threaded(A, x, X, sel, T)
     value = 2.0 * snnz * args.steps / dt
-    sample = ("every %d-th row (%d rows, %d nonzeros) per step, SpMV + SpMM(L=128) in binary64, single thread"
-              % (k, sel.size, snnz))
+    sample = ("every %d-th row (%d rows, %d nonzeros) per step, SpMV + SpMM(L=128) in binary64, rows dealt to %d "
+              "host threads" % (k, sel.size, snnz, T))
     print(json.dumps({
         "impl": "reference", "metric": "nonzeros/s", "value": value, "unit": "nnz/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload_name(args.scale), "nrows": A.nrows, "nnz": A.nnz, "L": L_COLS,
                    "units": "nonzeros processed (2 x nnz per step)",
-                   "reference": "the CPU oracle (binary64, one thread) on a row sample of the workload: " + sample},
-        "cpu_baseline": {"value": value, "unit": "nnz/s", "cores": 1, "kind": "oracle", "sample": sample},
+                   "reference": "the CPU oracle (binary64) on a row sample of the workload: " + sample},
+        "cpu_baseline": {"value": value, "unit": "nnz/s", "cores": T, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "nnz/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
