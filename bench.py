@@ -57,6 +57,10 @@ def parse_args(argv=None):
     p.add_argument("--rows", default="all",
                    help="comma list of extra hot-path rows to measure: cfg1,sddmm,backward,csf,batched,banded,spadd3,colblock "
                         "(or all, none)")
+    p.add_argument("--case", default="",
+                   help="time one kernel case alone and exit (for profiling): sddmm:K:DTYPE on the 2^20-row R-MAT "
+                        "with 32 samples per row, or spmttkrp:R:DTYPE on the Zipf CSF tensor (DTYPE f32, bf16 or "
+                        "f64; nnz split, unit 1024, 128 threads)")
     return p.parse_args(argv)
 
 
@@ -248,6 +252,40 @@ def error_stats(got, ref, scale):
     den = np.where(den == 0, 1.0, den)
     e = (np.abs(got - ref) / den).ravel()
     return {"max": float(e.max()) if e.size else 0.0, "p99": float(np.quantile(e, 0.99)) if e.size else 0.0}
+
+
+def run_case(args):
+    """One kernel case timed alone (3 untimed calls, then `--steps` calls between CUDA
+    events); prints one JSON line. Small enough to run under a profiler."""
+    import torch
+    import spd_synth
+    import paper_2207_13901_gb300 as spd
+    kind, width, dname = args.case.split(":")
+    width = int(width)
+    dt = {"f32": torch.float32, "bf16": torch.bfloat16, "f64": torch.float64}[dname]
+    tune = {"unit_items": 1024, "block_threads": 128}
+    if kind == "sddmm":
+        B = spd_synth.rmat_csr(20, 32, seed=0)
+        n = B.nrows
+        C = torch.from_numpy(spd_synth.normal((n, width), seed=10 + width, dtype=np.float32)).cuda().to(dt)
+        D = torch.from_numpy(spd_synth.normal((n, width), seed=20 + width, dtype=np.float32)).cuda().to(dt)
+        dB = spd.CSR.from_host(B.pos, B.crd, B.vals, (n, n), dtype=dt)
+        out = torch.empty(B.nnz, dtype=spd.result_dtype(dt), device="cuda")
+        fn = lambda: spd.sddmm(dB, C, D, out, split="nnz", tune=tune)
+        units, what = B.nnz, "SDDMM K=%d on R-MAT 2^20 (32 samples per row), %d nonzeros" % (width, B.nnz)
+    elif kind == "spmttkrp":
+        T = spd_synth.zipf_csf3((1 << 17,) * 3, 50_000_000, 1.1, seed=0)
+        dT = spd.CSF3.from_host(T.pos1, T.crd1, T.pos2, T.crd2, T.vals, T.dims, dtype=dt)
+        Cf = torch.from_numpy(spd_synth.normal((T.dims[1], width), seed=40 + width, dtype=np.float32)).cuda().to(dt)
+        Df = torch.from_numpy(spd_synth.normal((T.dims[2], width), seed=50 + width, dtype=np.float32)).cuda().to(dt)
+        Af = torch.empty((T.dims[0], width), dtype=spd.result_dtype(dt), device="cuda")
+        fn = lambda: spd.spmttkrp(dT, Cf, Df, Af, split="nnz", tune=tune)
+        units, what = T.nnz, "SpMTTKRP R=%d on the Zipf(1.1) CSF 2^17 x 2^17 x 2^17, %d nonzeros" % (width, T.nnz)
+    else:
+        raise SystemExit("unknown case %r" % args.case)
+    ms = _time_ms(fn, reps=max(1, args.steps), warm=3)
+    print(json.dumps({"case": args.case, "workload": what, "dtype": dname, "ms": round(ms, 4),
+                      "nnz_per_s": units / (ms * 1e-3), "tune": tune}))
 
 
 def run_gpu(args):
@@ -1104,6 +1142,8 @@ def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         run_reference(args)
+    elif args.case:
+        run_case(args)
     else:
         run_gpu(args)
 

@@ -13,6 +13,12 @@
 // step covers 32/G positions; U steps are in flight, and the U partial dot products of
 // a lane are reduced across the group together by a halving butterfly.
 //
+// When K fits in one or two k tiles of the group (KT = 1 or 2) a lane keeps its slice of
+// the current row of C in registers and loads C only in a warp step whose positions leave
+// that row (on the benchmarked R-MAT a row holds about 30 positions), and row addresses are
+// a 32-bit row index times a 32-bit byte pitch (one wide multiply-add). KT = 0 is the
+// general form for any K or pitch: both rows loaded per position, k tiles in a loop.
+//
 // The contraction over k is one dot product per stored position (a matrix-vector
 // shape, no reuse of D rows inside a warp), so it stays on the CUDA cores: at about
 // 0.5 flop per gathered byte it is bound by the gathers, not by arithmetic.
@@ -22,12 +28,12 @@ namespace spd {
 
 constexpr unsigned FULLM = 0xffffffffu;
 
-template <typename VT, int EPL, int G>
+template <typename VT, int EPL, int G, int KT>
 __global__ void __launch_bounds__(256) sddmm_warp_kernel(
     int64_t n, const int32_t *__restrict__ pos, const int32_t *__restrict__ crd, const VT *__restrict__ vals,
-    const VT *__restrict__ C, int64_t ldc, const VT *__restrict__ Dnk, int64_t ldd, int64_t K,
-    typename Traits<VT>::out *__restrict__ out, const int32_t *__restrict__ prow, const int32_t *__restrict__ ppos,
-    int64_t npieces, int64_t P) {
+    const VT *__restrict__ C, int64_t ldc, const VT *__restrict__ Dnk, int64_t ldd, int64_t K, uint32_t ldc_b,
+    uint32_t ldd_b, typename Traits<VT>::out *__restrict__ out, const int32_t *__restrict__ prow,
+    const int32_t *__restrict__ ppos, int64_t npieces, int64_t P) {
     using AT = typename Traits<VT>::acc;
     using OT = typename Traits<VT>::out;
     constexpr int NPG = 32 / G;                             // positions per warp step
@@ -47,6 +53,17 @@ __global__ void __launch_bounds__(256) sddmm_warp_kernel(
     bool writer;
     const int my_u = reduced_index<G, U>(gl, writer);
     const int64_t ktiles = (K + G * EPL - 1) / (G * EPL);
+    // KT > 0: byte offsets of this lane's slice, which k tiles it covers, and the cached
+    // slice of row `crow` of C
+    constexpr int NKT = KT > 0 ? KT : 1;
+    constexpr size_t TB = (size_t)G * EPL * sizeof(VT);
+    const char *Cl = reinterpret_cast<const char *>(C) + (size_t)gl * EPL * sizeof(VT);
+    const char *Dl = reinterpret_cast<const char *>(Dnk) + (size_t)gl * EPL * sizeof(VT);
+    bool kon[NKT];
+#pragma unroll
+    for (int kt = 0; kt < NKT; ++kt) kon[kt] = (int64_t)kt * G * EPL + (int64_t)gl * EPL < K;
+    XVec<VT, EPL> cc[NKT];
+    int32_t crow = -1;
 
     PosRows pr;
     pr.load(b.r0, n, pos, lane);
@@ -69,6 +86,54 @@ __global__ void __launch_bounds__(256) sddmm_warp_kernel(
             AT part[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) part[u] = 0;
+            if constexpr (KT > 0) {
+                // rows and columns of the step's positions; a position past the window
+                // repeats the last one (its product is zero and never written)
+                int32_t rr[U];
+                uint32_t dc[U];
+                bool ok[U];
+                bool same = true;
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int j = j0 + u * NPG + gi;
+                    ok[u] = j < cnt;
+                    const int jc = ok[u] ? j : cnt - 1;
+                    rr[u] = s_row[jc];
+                    dc[u] = (uint32_t)s_crd[jc];
+                    same = same && rr[u] == crow;
+                }
+#pragma unroll
+                for (int kt = 0; kt < KT; ++kt) {
+                    if (!kon[kt]) continue;
+                    XVec<VT, EPL> dv[U];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        if (ok[u]) dv[u].load(reinterpret_cast<const VT *>(Dl + kt * TB + (uint64_t)dc[u] * ldd_b));
+                        else dv[u].clear();
+                    }
+                    if (same) {
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+#pragma unroll
+                            for (int e = 0; e < EPL; ++e)
+                                part[u] = fma((AT)cc[kt].at(e), (AT)dv[u].at(e), part[u]);
+                        }
+                    } else {
+                        XVec<VT, EPL> cv[U];
+#pragma unroll
+                        for (int u = 0; u < U; ++u)
+                            cv[u].load(reinterpret_cast<const VT *>(Cl + kt * TB + (uint64_t)(uint32_t)rr[u] * ldc_b));
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+#pragma unroll
+                            for (int e = 0; e < EPL; ++e)
+                                part[u] = fma((AT)cv[u].at(e), (AT)dv[u].at(e), part[u]);
+                        }
+                        cc[kt] = cv[U - 1];
+                    }
+                }
+                crow = rr[U - 1];
+            } else {
 #pragma unroll 1
             for (int64_t kt = 0; kt < ktiles; ++kt) {
                 const int64_t k = kt * (G * EPL) + (int64_t)gl * EPL;
@@ -92,6 +157,7 @@ __global__ void __launch_bounds__(256) sddmm_warp_kernel(
                     }
                 }
             }
+            }
             const AT tot = group_reduce<G, U>(part, gl);
             const int j = j0 + my_u * NPG + gi;
             if (writer && j < cnt) __stcs(out + pb + j, (OT)(s_val[j] * tot));
@@ -99,10 +165,11 @@ __global__ void __launch_bounds__(256) sddmm_warp_kernel(
     }
 }
 
-template <typename VT, int EPL, int G>
+template <typename VT, int EPL, int G, int KT>
 static spd_status launch_sddmm_g(const spd_csr *B, const void *C, int64_t K, int64_t ldc, const void *Dnk,
                                  int64_t ldd, void *outv, int split, const Tuning &tn, void *ws, cudaStream_t st) {
     using OT = typename Traits<VT>::out;
+    const uint32_t ldc_b = (uint32_t)(ldc * (int64_t)sizeof(VT)), ldd_b = (uint32_t)(ldd * (int64_t)sizeof(VT));
     const int threads = tn.block_threads > 256 ? 256 : tn.block_threads;  // shared windows for <= 8 warps
     const int wpb = threads / 32;
     const VT *v = static_cast<const VT *>(B->vals);
@@ -112,8 +179,8 @@ static spd_status launch_sddmm_g(const spd_csr *B, const void *C, int64_t K, int
     if (split == SPD_SPLIT_ROW) {
         int64_t P = tn.row_pieces > 0 ? tn.row_pieces : ceil_div(B->nrows + B->nnz, tn.unit_items);
         if (P < 1) P = 1;
-        sddmm_warp_kernel<VT, EPL, G><<<(unsigned)ceil_div(P, wpb), threads, 0, st>>>(
-            B->nrows, B->pos, B->crd, v, cc, ldc, dd, ldd, K, o, nullptr, nullptr, 0, P);
+        sddmm_warp_kernel<VT, EPL, G, KT><<<(unsigned)ceil_div(P, wpb), threads, 0, st>>>(
+            B->nrows, B->pos, B->crd, v, cc, ldc, dd, ldd, K, ldc_b, ldd_b, o, nullptr, nullptr, 0, P);
         return check_launch("sddmm_warp_kernel(row)");
     }
     WsLayout Lw = layout_warp(B->nrows, B->nnz, split, tn.unit_items, 0, false);
@@ -122,9 +189,27 @@ static spd_status launch_sddmm_g(const spd_csr *B, const void *C, int64_t K, int
     int32_t *ppos = reinterpret_cast<int32_t *>(w + Lw.part_pos);
     spd_status s = launch_merge_partition(B->nrows, B->nnz, B->pos, tn.unit_items, Lw.npieces, prow, ppos, st);
     if (s) return s;
-    sddmm_warp_kernel<VT, EPL, G><<<(unsigned)ceil_div(Lw.npieces, wpb), threads, 0, st>>>(
-        B->nrows, B->pos, B->crd, v, cc, ldc, dd, ldd, K, o, prow, ppos, Lw.npieces, 0);
+    sddmm_warp_kernel<VT, EPL, G, KT><<<(unsigned)ceil_div(Lw.npieces, wpb), threads, 0, st>>>(
+        B->nrows, B->pos, B->crd, v, cc, ldc, dd, ldd, K, ldc_b, ldd_b, o, prow, ppos, Lw.npieces, 0);
     return check_launch("sddmm_warp_kernel(nnz)");
+}
+
+// The cached-row form (KT = 1 or 2 k tiles) needs 16-byte vectors and row pitches below
+// 4 GiB; anything else takes the general form (KT = 0).
+template <typename VT, int EPL, int G>
+static spd_status launch_sddmm_kt(const spd_csr *B, const void *C, int64_t K, int64_t ldc, const void *Dnk,
+                                  int64_t ldd, void *outv, int split, const Tuning &tn, void *ws, cudaStream_t st) {
+    if constexpr (EPL * sizeof(VT) == 16) {
+        const int64_t pitch_max = (int64_t)UINT32_MAX / (int64_t)sizeof(VT);
+        if (ldc <= pitch_max && ldd <= pitch_max) {
+            const int64_t kt = ceil_div(K > 0 ? K : 1, (int64_t)G * EPL);
+            if (kt == 1) return launch_sddmm_g<VT, EPL, G, 1>(B, C, K, ldc, Dnk, ldd, outv, split, tn, ws, st);
+            if constexpr (G == 32) {
+                if (kt == 2) return launch_sddmm_g<VT, EPL, G, 2>(B, C, K, ldc, Dnk, ldd, outv, split, tn, ws, st);
+            }
+        }
+    }
+    return launch_sddmm_g<VT, EPL, G, 0>(B, C, K, ldc, Dnk, ldd, outv, split, tn, ws, st);
 }
 
 // Group width: the power of two in [4, 32] closest to covering K with EPL-element vectors.
@@ -132,10 +217,10 @@ template <typename VT, int EPL>
 static spd_status launch_sddmm_epl(const spd_csr *B, const void *C, int64_t K, int64_t ldc, const void *Dnk,
                                    int64_t ldd, void *outv, int split, const Tuning &tn, void *ws, cudaStream_t st) {
     const int64_t lanes = ceil_div(K > 0 ? K : 1, EPL);
-    if (lanes <= 4) return launch_sddmm_g<VT, EPL, 4>(B, C, K, ldc, Dnk, ldd, outv, split, tn, ws, st);
-    if (lanes <= 8) return launch_sddmm_g<VT, EPL, 8>(B, C, K, ldc, Dnk, ldd, outv, split, tn, ws, st);
-    if (lanes <= 16) return launch_sddmm_g<VT, EPL, 16>(B, C, K, ldc, Dnk, ldd, outv, split, tn, ws, st);
-    return launch_sddmm_g<VT, EPL, 32>(B, C, K, ldc, Dnk, ldd, outv, split, tn, ws, st);
+    if (lanes <= 4) return launch_sddmm_kt<VT, EPL, 4>(B, C, K, ldc, Dnk, ldd, outv, split, tn, ws, st);
+    if (lanes <= 8) return launch_sddmm_kt<VT, EPL, 8>(B, C, K, ldc, Dnk, ldd, outv, split, tn, ws, st);
+    if (lanes <= 16) return launch_sddmm_kt<VT, EPL, 16>(B, C, K, ldc, Dnk, ldd, outv, split, tn, ws, st);
+    return launch_sddmm_kt<VT, EPL, 32>(B, C, K, ldc, Dnk, ldd, outv, split, tn, ws, st);
 }
 
 template <typename VT>

@@ -247,7 +247,7 @@ def test_spmm_t(name, dtype, L):
 
 @pytest.mark.parametrize("name", ["uniform4096", "rmat12", "longrow", "col0", "no_nnz"])
 @pytest.mark.parametrize("dtype", DTYPES)
-@pytest.mark.parametrize("K", [1, 32, 128, 256, 300])
+@pytest.mark.parametrize("K", [1, 6, 24, 32, 48, 128, 200, 256, 300])
 def test_sddmm(name, dtype, K):
     A = get_mats()[name]
     rng = np.random.default_rng(15)
@@ -273,6 +273,29 @@ def test_sddmm(name, dtype, K):
     scale1 = oracle.sddmm(A.pos, A.crd, None, np.abs(Cr), np.abs(Dr), sel=sel)
     out = spd.sddmm(dA.with_vals(None), dC, dD).double().cpu().numpy()
     check(out if sel is None else out[sel], ref1, scale1, dtype, "sddmm pattern %s" % name)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("K", [40, 128, 200])
+def test_sddmm_strided_operands(dtype, K):
+    """C and Dnk as column windows of wider row-major matrices (leading dimension > K,
+    starting 16 elements in), for the register-cached and the general forms."""
+    A = get_mats()["rmat12"]
+    rng = np.random.default_rng(16)
+    C = rng.standard_normal((A.nrows, K))
+    Dnk = rng.standard_normal((A.ncols, K))
+    vr, Cr, Dr = rounded(A.vals, dtype), rounded(C, dtype), rounded(Dnk, dtype)
+    ref = oracle.sddmm(A.pos, A.crd, vr, Cr, Dr, accurate=True)
+    scale = oracle.sddmm(A.pos, A.crd, np.abs(vr), np.abs(Cr), np.abs(Dr))
+    wideC = torch.zeros((A.nrows, K + 48), dtype=dtype, device="cuda")
+    wideD = torch.zeros((A.ncols, K + 32), dtype=dtype, device="cuda")
+    wideC[:, 16:16 + K] = dev(C, dtype)
+    wideD[:, 16:16 + K] = dev(Dnk, dtype)
+    dA = dev_csr(A, dtype)
+    for split in SPLITS:
+        out = spd.sddmm(dA, wideC[:, 16:16 + K], wideD[:, 16:16 + K], split=split)
+        torch.cuda.synchronize()
+        check(out.double().cpu().numpy(), ref, scale, dtype, "sddmm strided %s K=%d %s" % (dtype, K, split))
 
 
 # ------------------------------------------------------------------------------ CSF kernels
