@@ -344,7 +344,8 @@ spd_status spd_spttv(const spd_csf3 *B, const void *c, int c_type, void *out_val
                      int split, const spd_tune *tune, void *ws, size_t ws_bytes, void *stream);
 
 /* SpMTTKRP A(i,l) = B(i,j,k) * C(j,l) * D(k,l), l < R.  C: dim1 x R (ldc), D: dim2 x R
- * (ldd) of factor_type == B->vtype; A: dim0 x R (lda) of a_type. */
+ * (ldd) of factor_type == B->vtype; A: dim0 x R (lda) of a_type. A row stride of C or D
+ * of 4 GiB or more returns SPD_ERR_SHAPE. */
 spd_status spd_spmttkrp(const spd_csf3 *B, const void *C, int64_t ldc, const void *D, int64_t ldd,
                         int64_t R, int factor_type, void *A, int64_t lda, int a_type, int split,
                         const spd_tune *tune, void *ws, size_t ws_bytes, void *stream);

@@ -15,7 +15,10 @@
 //     is a binary64 carry added by the fix-up kernel.
 //   Row split: universe partition of the slices, [floor(c I/P), floor((c+1) I/P)).
 // The contraction per entry is a scaled row of D (no dense reuse within a warp), so the
-// work stays on the CUDA cores.
+// work stays on the CUDA cores. The kernel is bound by instruction issue (the factor rows
+// come from L2), so rows are addressed as a 32-bit index times a 32-bit byte pitch (one
+// wide multiply-add) and warp steps that lie wholly inside a slice segment skip the
+// per-entry bounds checks.
 #include "spd_internal.cuh"
 
 namespace spd {
@@ -48,7 +51,7 @@ template <typename VT, int EPL, int G>
 __global__ void __launch_bounds__(256) spmttkrp_warp_kernel(
     int64_t I, int64_t F, const int32_t *__restrict__ pos1, const int32_t *__restrict__ crd1,
     const int32_t *__restrict__ pos2, const int32_t *__restrict__ crd2, const VT *__restrict__ vals,
-    const VT *__restrict__ C, int64_t ldc, const VT *__restrict__ D, int64_t ldd, int64_t R,
+    const VT *__restrict__ C, uint32_t ldc_b, const VT *__restrict__ D, uint32_t ldd_b, int64_t R,
     typename Traits<VT>::out *__restrict__ A, int64_t lda, const int32_t *__restrict__ pfib,
     const int32_t *__restrict__ ppos, const int32_t *__restrict__ pslice, int64_t npieces, int64_t P,
     int32_t *__restrict__ carry_row, double *__restrict__ carry_val) {
@@ -65,6 +68,8 @@ __global__ void __launch_bounds__(256) spmttkrp_warp_kernel(
     const int gi = lane / G, gl = lane % G;
     const int64_t col = (int64_t)blockIdx.y * (G * EPL) + (int64_t)gl * EPL;
     const bool active = col < R;
+    const char *Cl = reinterpret_cast<const char *>(C) + (size_t)col * sizeof(VT);
+    const char *Dl = reinterpret_cast<const char *>(D) + (size_t)col * sizeof(VT);
 
     int32_t f0, p0, f1, p1, s0, s1;
     if (pfib) {
@@ -151,23 +156,38 @@ __global__ void __launch_bounds__(256) spmttkrp_warp_kernel(
 #pragma unroll 1
             for (int t0 = a; t0 < bnd; t0 += NPG * U) {
                 XVec<VT, EPL> cv[U], dv[U];  // bfloat16 stays packed until the multiply
+                AT v[U];
+                if (t0 + NPG * U <= bnd) {  // every entry of the step lies in the segment
 #pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int j = t0 + u * NPG + gi;
-                    if (active && j < bnd) {
-                        cv[u].load(C + (int64_t)s_j[j] * ldc + col);
-                        dv[u].load(D + (int64_t)s_k[j] * ldd + col);
-                    } else {
-                        cv[u].clear();
-                        dv[u].clear();
+                    for (int u = 0; u < U; ++u) {
+                        const int j = t0 + u * NPG + gi;
+                        v[u] = s_v[j];
+                        if (active) {
+                            cv[u].load(reinterpret_cast<const VT *>(Cl + (uint64_t)(uint32_t)s_j[j] * ldc_b));
+                            dv[u].load(reinterpret_cast<const VT *>(Dl + (uint64_t)(uint32_t)s_k[j] * ldd_b));
+                        } else {
+                            cv[u].clear();
+                            dv[u].clear();
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const int j = t0 + u * NPG + gi;
+                        v[u] = j < bnd ? s_v[j] : (AT)0;
+                        if (active && j < bnd) {
+                            cv[u].load(reinterpret_cast<const VT *>(Cl + (uint64_t)(uint32_t)s_j[j] * ldc_b));
+                            dv[u].load(reinterpret_cast<const VT *>(Dl + (uint64_t)(uint32_t)s_k[j] * ldd_b));
+                        } else {
+                            cv[u].clear();
+                            dv[u].clear();
+                        }
                     }
                 }
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
-                    const int j = t0 + u * NPG + gi;
-                    const AT v = j < bnd ? s_v[j] : (AT)0;
 #pragma unroll
-                    for (int e = 0; e < EPL; ++e) acc[e] = fma(v * (AT)cv[u].at(e), (AT)dv[u].at(e), acc[e]);
+                    for (int e = 0; e < EPL; ++e) acc[e] = fma(v[u] * (AT)cv[u].at(e), (AT)dv[u].at(e), acc[e]);
                 }
             }
             dirty = true;
@@ -197,6 +217,7 @@ static spd_status launch_mttkrp_g(const spd_csf3 *B, const void *C, int64_t ldc,
     const int threads = tn.block_threads > 256 ? 256 : tn.block_threads;  // shared windows for <= 8 warps
     const int wpb = threads / 32;
     const int64_t ctiles = ceil_div(R, G * EPL);
+    const uint32_t ldc_b = (uint32_t)(ldc * (int64_t)sizeof(VT)), ldd_b = (uint32_t)(ldd * (int64_t)sizeof(VT));
     const VT *v = static_cast<const VT *>(B->vals);
     const VT *cc = static_cast<const VT *>(C);
     const VT *dd = static_cast<const VT *>(D);
@@ -208,8 +229,8 @@ static spd_status launch_mttkrp_g(const spd_csf3 *B, const void *C, int64_t ldc,
         if (P < 1) P = 1;
         dim3 grid((unsigned)ceil_div(P, wpb), (unsigned)ctiles);
         spmttkrp_warp_kernel<VT, EPL, G><<<grid, threads, 0, st>>>(
-            B->dim0, B->nfib, B->pos1, B->crd1, B->pos2, B->crd2, v, cc, ldc, dd, ldd, R, aa, lda, nullptr, nullptr,
-            nullptr, 0, P, nullptr, nullptr);
+            B->dim0, B->nfib, B->pos1, B->crd1, B->pos2, B->crd2, v, cc, ldc_b, dd, ldd_b, R, aa, lda, nullptr,
+            nullptr, nullptr, 0, P, nullptr, nullptr);
         return check_launch("spmttkrp_warp_kernel(row)");
     }
     WsLayout Lw = layout_mttkrp(B->nfib, B->nnz, split, tn.unit_items, R);
@@ -226,7 +247,7 @@ static spd_status launch_mttkrp_g(const spd_csf3 *B, const void *C, int64_t ldc,
     if ((s = check_launch("slice_partition_kernel"))) return s;
     dim3 grid((unsigned)ceil_div(Lw.npieces, wpb), (unsigned)ctiles);
     spmttkrp_warp_kernel<VT, EPL, G><<<grid, threads, 0, st>>>(
-        B->dim0, B->nfib, B->pos1, B->crd1, B->pos2, B->crd2, v, cc, ldc, dd, ldd, R, aa, lda, pfib, ppos, psl,
+        B->dim0, B->nfib, B->pos1, B->crd1, B->pos2, B->crd2, v, cc, ldc_b, dd, ldd_b, R, aa, lda, pfib, ppos, psl,
         Lw.npieces, 0, crow, cval);
     if ((s = check_launch("spmttkrp_warp_kernel(nnz)"))) return s;
     return launch_carry_fixup<OT>(Lw.npieces, R, crow, cval, reinterpret_cast<int32_t *>(w + Lw.chunk_row),
@@ -270,6 +291,8 @@ extern "C" spd_status spd_spmttkrp(const spd_csf3 *B, const void *C, int64_t ldc
     if ((s = check_dense("C", C, B->dim1, R, ldc, factor_type))) return s;
     if ((s = check_dense("D", D, B->dim2, R, ldd, factor_type))) return s;
     if ((s = check_dense("A", A, B->dim0, R, lda, a_type))) return s;
+    if ((uint64_t)ldc * dtype_size(factor_type) > UINT32_MAX || (uint64_t)ldd * dtype_size(factor_type) > UINT32_MAX)
+        return fail(SPD_ERR_SHAPE, "C or D row stride exceeds 4 GiB");
     Tuning tn;
     if ((s = read_tune(tune, &tn))) return s;
     split = resolve_split(split);

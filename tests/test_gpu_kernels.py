@@ -355,6 +355,29 @@ def test_spmttkrp(name, dtype, R):
         check(A.double().cpu().numpy(), ref, scale, dtype, "spmttkrp %s %s R=%d %s %s" % (name, dtype, R, split, tune))
 
 
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("R", [32, 40])
+def test_spmttkrp_strided_factors(dtype, R):
+    """C and D as column windows of wider row-major matrices (leading dimension R + 24,
+    starting 8 elements in)."""
+    T = get_tens()["zipf"]
+    rng = np.random.default_rng(24)
+    C = rng.standard_normal((T.dims[1], R))
+    D = rng.standard_normal((T.dims[2], R))
+    vr, Cr, Dr = rounded(T.vals, dtype), rounded(C, dtype), rounded(D, dtype)
+    ref = oracle.spmttkrp(T.pos1, T.crd1, T.pos2, T.crd2, vr, Cr, Dr, accurate=True)
+    scale = oracle.spmttkrp(T.pos1, T.crd1, T.pos2, T.crd2, np.abs(vr), np.abs(Cr), np.abs(Dr))
+    wideC = torch.zeros((T.dims[1], R + 24), dtype=dtype, device="cuda")
+    wideD = torch.zeros((T.dims[2], R + 24), dtype=dtype, device="cuda")
+    wideC[:, 8:8 + R] = dev(C, dtype)
+    wideD[:, 8:8 + R] = dev(D, dtype)
+    dT = dev_csf(T, dtype)
+    for split in SPLITS:
+        A = spd.spmttkrp(dT, wideC[:, 8:8 + R], wideD[:, 8:8 + R], split=split)
+        torch.cuda.synchronize()
+        check(A.double().cpu().numpy(), ref, scale, dtype, "spmttkrp strided %s R=%d %s" % (dtype, R, split))
+
+
 # ------------------------------------------------------------------------------ autograd
 
 def test_spmm_autograd_matches_oracle_gradients_and_finite_differences():
