@@ -9,6 +9,10 @@ with the host C compiler and marshals numpy arrays through ctypes.
 Every function takes numpy arrays (int32 structure, values upcast to float64) and
 returns float64 results. ``sel`` selects a subset of outputs for sampled checks on
 large inputs.
+
+The environment variable ``SPD_ORACLE_LIB`` names a compiled copy of the oracle to load
+instead of building this one; the mutation test uses it to run the pins against copies
+with a planted mistake.
 """
 from __future__ import annotations
 
@@ -72,7 +76,7 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            path = build()
+            path = os.environ.get("SPD_ORACLE_LIB") or build()
             L = ctypes.CDLL(path)
             for name, args in _SIGS.items():
                 fn = getattr(L, name)
