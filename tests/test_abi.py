@@ -186,3 +186,16 @@ def test_product_path_has_no_oracle_dependency():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text and "spd_oracle" not in text, f
+
+
+def test_host_tensors_are_refused():
+    """No CPU path: every binding refuses host tensors before calling the library."""
+    import torch
+    import paper_2207_13901_gb300 as spd
+    pos = torch.tensor([0, 1, 2], dtype=torch.int32)
+    crd = torch.tensor([0, 1], dtype=torch.int32)
+    vals = torch.ones(2)
+    with pytest.raises(TypeError, match="no CPU path"):
+        spd.CSR(pos, crd, vals, (2, 2))
+    with pytest.raises(TypeError, match="no CPU path"):
+        spd.CSF3(pos, crd, pos, crd, vals, (2, 2, 2))
