@@ -54,6 +54,27 @@ MUTANTS = [
      "v = have ? v + t : t; ++pd;", "v = t; ++pd;"),
     ("column blocks take an inclusive upper bound",
      "crd[p] < bounds[b + 1]", "crd[p] <= bounds[b + 1]"),
+    ("compensated SpMV returns only its leading part",
+     "csum_add_prod(&acc, vals[jB], x[crd[jB]]);\n        y[t] = csum_value(&acc);",
+     "csum_add_prod(&acc, vals[jB], x[crd[jB]]);\n        y[t] = acc.hi;"),
+    ("compensated SpMM returns only its leading part",
+     "for (int64_t l = 0; l < L; ++l) Y[t * ldy + l] = csum_value(&acc[l]);",
+     "for (int64_t l = 0; l < L; ++l) Y[t * ldy + l] = acc[l].hi;"),
+    ("compensated SpMM^T drops the final fold of its low parts",
+     "for (int64_t l = 0; l < L; ++l) dX[j * ldx + l] += lo[j * L + l];",
+     "for (int64_t l = 0; l < L; ++l) dX[j * ldx + l] += 0.0 * lo[j * L + l];"),
+    ("compensated SDDMM drops the rounding error of B*C",
+     "csum_add_prod3(&acc, b, C[i * ldc + k], Dnk[j * ldd + k]);",
+     "csum_add_prod(&acc, b * C[i * ldc + k], Dnk[j * ldd + k]);"),
+    ("compensated SDDMM returns only its leading part",
+     "csum_add_prod3(&acc, b, C[i * ldc + k], Dnk[j * ldd + k]);\n        out[t] = csum_value(&acc);",
+     "csum_add_prod3(&acc, b, C[i * ldc + k], Dnk[j * ldd + k]);\n        out[t] = acc.hi;"),
+    ("compensated SpTTV returns only its leading part",
+     "csum_add_prod(&acc, vals[p], c[crd2[p]]);\n        out[t] = csum_value(&acc);",
+     "csum_add_prod(&acc, vals[p], c[crd2[p]]);\n        out[t] = acc.hi;"),
+    ("compensated SpMTTKRP returns only its leading part",
+     "for (int64_t l = 0; l < R; ++l) A[t * lda + l] = csum_value(&acc[l]);",
+     "for (int64_t l = 0; l < R; ++l) A[t * lda + l] = acc[l].hi;"),
 ]
 
 

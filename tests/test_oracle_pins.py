@@ -332,6 +332,158 @@ def test_triple_product_compensation_under_cancellation():
     assert abs(Fraction(got) - ex) <= Fraction(4 * 2.0 ** -53) * abs(ex)
 
 
+# ------------------------------------------------------------------------------ compensated variants under cancellation
+#
+# Each case below sums terms of size ~1e8 that cancel to a result of order 1, so a
+# binary64 running sum loses about 1e-8 per addition: only a compensated sum meets the
+# Dot2 bound |res - s| <= u|s| + gamma_m^2 * sum|t| (Ogita, Rump and Oishi 2005, Prop. 5.5;
+# u = 2^-53). The exact value is the sum of the rational products of the binary64 inputs.
+# A compensated variant that returns only its leading part, drops a low-order fold or an
+# error term of a product, or accumulates in the wrong place fails these bounds.
+
+U53 = 2.0 ** -53
+
+
+def _gamma(m):
+    return (m * U53) / (1 - m * U53)
+
+
+def _cancelling(rng, h, q, big=1e8):
+    """h pairs (v, -v(1+d)) of magnitude ~big plus q terms in [-1, 1): the pairs leave
+    residues of about big*d, the sum is of order one while partial sums reach ~big."""
+    v = rng.uniform(0.5, 1.0, h) * big * rng.choice([-1.0, 1.0], h)
+    d = rng.uniform(1e-14, 1e-13, h)
+    return v, -v * (1 + d), rng.uniform(-1, 1, q)
+
+
+def _dot2_ok(got, exact, absum, m, extra=Fraction(0)):
+    bound = Fraction(U53) * abs(exact) + Fraction(_gamma(m) ** 2 * absum) + extra
+    return abs(Fraction(float(got)) - exact) <= bound
+
+
+def _fr(a):
+    return Fraction(float(a))
+
+
+@pytest.mark.parametrize("seed", SEEDS)
+def test_spmm_acc_against_exact_rationals_under_cancellation(seed):
+    rng = np.random.default_rng(600 + seed)
+    h, q, L = 120, 24, 3
+    m = 2 * h + q
+    va, vb, vq = _cancelling(rng, h, q)
+    cols = rng.permutation(m)
+    ca, cb, cq = cols[:h], cols[h:2 * h], cols[2 * h:]
+    vals_of_col = np.empty(m)
+    vals_of_col[ca], vals_of_col[cb], vals_of_col[cq] = va, vb, vq
+    X = rng.uniform(0.5, 1.5, (m, L))
+    X[cb] = X[ca]  # each pair multiplies the same row of X
+    # row 1 holds the cancelling sum; rows 0 and 2 are short and well conditioned
+    rows = np.concatenate([[0, 0], np.ones(m, dtype=np.int64), [2]])
+    cc = np.concatenate([[3, 7], np.arange(m), [5]])
+    vv = np.concatenate([[0.25, -0.5], vals_of_col, [0.75]])
+    A = spd_synth.csr_from_coords(3, m, rows, cc, vals=vv)
+    got = oracle.spmm(A.pos, A.crd, A.vals, X, accurate=True)
+    for i in range(3):
+        for l in range(L):
+            terms = [_fr(A.vals[p]) * _fr(X[A.crd[p], l]) for p in range(A.pos[i], A.pos[i + 1])]
+            exact = sum(terms, Fraction(0))
+            absum = float(sum(abs(t) for t in terms))
+            assert _dot2_ok(got[i, l], exact, absum, len(terms)), (i, l)
+    # the plain oracle on row 1 is far from exact (the case is really ill-conditioned)
+    plain = oracle.spmm(A.pos, A.crd, A.vals, X)
+    ex1 = sum((_fr(A.vals[p]) * _fr(X[A.crd[p], 0]) for p in range(A.pos[1], A.pos[2])), Fraction(0))
+    assert abs(Fraction(float(plain[1, 0])) - ex1) > 1e6 * Fraction(U53) * abs(ex1)
+
+
+@pytest.mark.parametrize("seed", SEEDS)
+def test_spmm_t_acc_against_exact_rationals_under_cancellation(seed):
+    rng = np.random.default_rng(700 + seed)
+    h, q, L = 120, 24, 3
+    n = 2 * h + q
+    va, vb, vq = _cancelling(rng, h, q)
+    rows_perm = rng.permutation(n)
+    ra, rb, rq = rows_perm[:h], rows_perm[h:2 * h], rows_perm[2 * h:]
+    vals_of_row = np.empty(n)
+    vals_of_row[ra], vals_of_row[rb], vals_of_row[rq] = va, vb, vq
+    dY = rng.uniform(0.5, 1.5, (n, L))
+    dY[rb] = dY[ra]
+    # column 1 of A gathers the cancelling entries (one per row); column 0 a few others
+    rows = np.concatenate([np.arange(n), [4, 9, 30]])
+    cols = np.concatenate([np.ones(n, dtype=np.int64), [0, 0, 0]])
+    vals = np.concatenate([vals_of_row, [0.5, -1.25, 0.75]])
+    A = spd_synth.csr_from_coords(n, 3, rows, cols, vals=vals)
+    got = oracle.spmm_t(A.pos, A.crd, A.vals, dY, 3, accurate=True)
+    for j in range(3):
+        for l in range(L):
+            terms = [_fr(A.vals[p]) * _fr(dY[i, l]) for i in range(n) for p in range(A.pos[i], A.pos[i + 1])
+                     if A.crd[p] == j]
+            exact = sum(terms, Fraction(0))
+            absum = float(sum(abs(t) for t in terms))
+            assert _dot2_ok(got[j, l], exact, absum, max(len(terms), 1)), (j, l)
+    assert got[2].tolist() == [0.0] * L  # a column without entries
+
+
+@pytest.mark.parametrize("seed", SEEDS)
+def test_sddmm_acc_against_exact_rationals_under_cancellation(seed):
+    rng = np.random.default_rng(800 + seed)
+    h, q = 100, 20
+    K = 2 * h + q
+    ks = rng.permutation(K)
+    ka, kb, kq = ks[:h], ks[h:2 * h], ks[2 * h:]
+    n, m = 3, 4
+    C = rng.uniform(-1, 1, (n, K))
+    for i in range(n):  # every row of C cancels over k against every row of Dnk
+        va, vb, vq = _cancelling(rng, h, q)
+        C[i, ka], C[i, kb], C[i, kq] = va, vb, vq
+    Dnk = rng.uniform(0.5, 1.5, (m, K))
+    Dnk[:, kb] = Dnk[:, ka]
+    rows = np.array([0, 0, 1, 2, 2, 2])
+    cols = np.array([1, 3, 0, 0, 2, 3])
+    b = rng.uniform(0.5, 1.5, rows.shape[0]) * 0.7  # products b*C are inexact in binary64
+    B = spd_synth.csr_from_coords(n, m, rows, cols, vals=b)
+    got = oracle.sddmm(B.pos, B.crd, B.vals, C, Dnk, accurate=True)
+    got_sel = oracle.sddmm(B.pos, B.crd, B.vals, C, Dnk, sel=np.array([4, 0, 2]), accurate=True)
+    ri = np.repeat(np.arange(n), np.diff(B.pos))
+    for p in range(B.nnz):
+        i, j = ri[p], B.crd[p]
+        terms = [_fr(B.vals[p]) * _fr(C[i, k]) * _fr(Dnk[j, k]) for k in range(K)]
+        exact = sum(terms, Fraction(0))
+        absum = float(sum(abs(t) for t in terms))
+        # the triple product's second-order term e*c is rounded once: u^2 per term
+        extra = Fraction(U53) * abs(exact) + Fraction(2 * U53 * U53 * absum)
+        assert _dot2_ok(got[p], exact, absum, K, extra), p
+    assert got_sel.tolist() == [got[4], got[0], got[2]]
+
+
+@pytest.mark.parametrize("seed", SEEDS)
+def test_spttv_acc_against_exact_rationals_under_cancellation(seed):
+    rng = np.random.default_rng(900 + seed)
+    h, q = 120, 24
+    m = 2 * h + q
+    va, vb, vq = _cancelling(rng, h, q)
+    ks = rng.permutation(m)
+    ka, kb, kq = ks[:h], ks[h:2 * h], ks[2 * h:]
+    vals_of_k = np.empty(m)
+    vals_of_k[ka], vals_of_k[kb], vals_of_k[kq] = va, vb, vq
+    c = rng.uniform(0.5, 1.5, m)
+    c[kb] = c[ka]
+    # fiber (0, 1) holds the cancelling sum; fibers (0, 0) and (1, 2) are short
+    i = np.concatenate([[0, 0], np.zeros(m, dtype=np.int64), [1, 1]])
+    j = np.concatenate([[0, 0], np.ones(m, dtype=np.int64), [2, 2]])
+    k = np.concatenate([[4, 9], np.arange(m), [1, 3]])
+    v = np.concatenate([[0.5, -0.25], vals_of_k, [1.5, -0.75]])
+    T = spd_synth.csf3_from_coords((2, 3, m), i, j, k, v)
+    got = oracle.spttv(T.pos1, T.crd1, T.pos2, T.crd2, T.vals, c, accurate=True)
+    for f in range(T.nfib):
+        terms = [_fr(T.vals[p]) * _fr(c[T.crd2[p]]) for p in range(T.pos2[f], T.pos2[f + 1])]
+        exact = sum(terms, Fraction(0))
+        absum = float(sum(abs(t) for t in terms))
+        assert _dot2_ok(got[f], exact, absum, len(terms)), f
+    plain = oracle.spttv(T.pos1, T.crd1, T.pos2, T.crd2, T.vals, c)
+    ex1 = sum((_fr(T.vals[p]) * _fr(c[T.crd2[p]]) for p in range(T.pos2[1], T.pos2[2])), Fraction(0))
+    assert abs(Fraction(float(plain[1])) - ex1) > 1e6 * Fraction(U53) * abs(ex1)
+
+
 # ------------------------------------------------------------------------------ partitions
 
 def _random_pos(rng, n, maxlen):
