@@ -405,9 +405,12 @@ spd_status spd_spmm_batched_run(const spd_batch_plan *plan, void *stream);
  *   - Limit: the scratch must hold what spd_csr_workspace_size(SPD_OP_SPMV, A,
  *     SPD_SPLIT_NNZ, ...) reports, about 20 bytes per 2048 items, so nrows + nnz up to
  *     about 107 million fits; larger inputs return SPD_ERR_SHAPE before any launch.
- *   - The first call on a device looks up the array's device address with
- *     cudaGetSymbolAddress (with that device current) and caches it; make that first
- *     call before any stream capture.
+ *   - The array exists once per CUDA context that loads the library. The first call
+ *     in a context (the current one of the calling thread, e.g. a device's primary
+ *     context or a context the caller made current with the driver API) looks up the
+ *     array's device address with cudaGetSymbolAddress and caches it under the
+ *     context's unique id. Make that first call before any stream capture: while the
+ *     stream is being captured it returns SPD_ERR_ARG.
  *   - All calls share the one array, which keeps the last call's contents. Each call
  *     writes every scratch byte before reading it, so no clearing is needed, but calls
  *     whose GPU work overlaps (different streams, or different threads) race on the

@@ -84,3 +84,37 @@ def normalized_error(got, ref, scale):
     denom = np.maximum(np.abs(ref), np.asarray(scale, dtype=np.float64))
     denom = np.where(denom == 0, 1.0, denom)
     return np.abs(got - ref) / denom
+
+
+U24 = 2.0 ** -24  # unit roundoff of binary32
+
+
+def binary32_gate(nterms, extra=0.0):
+    """Error gate of an output summed from n terms with binary32 accumulation, relative
+    to the normaliser of ``normalized_error``: (2 log2 n + 2 + extra) * 2^-24, i.e.
+    2 + extra units for a single term. The 2 log2 n units allow a summation tree (a
+    per-thread or per-lane run plus a shuffle or scan tree, each about log2 n deep); the
+    2 units cover the rounding of each product and of the result; ``extra`` adds units
+    for statements whose terms are rounded more than once (triple products)."""
+    n = np.maximum(np.asarray(nterms, dtype=np.float64), 1.0)
+    return (2.0 * np.log2(n) + 2.0 + extra) * U24
+
+
+def check_error(got, ref, scale, binary64, nterms, what, extra=0.0):
+    """Asserts the normalised error of every output: <= 1e-12 for binary64 results,
+    <= binary32_gate(nterms) otherwise (nterms broadcast against the outputs). Returns
+    the largest normalised error."""
+    err = normalized_error(got, ref, scale)
+    if err.size == 0:
+        return 0.0
+    tol = np.full(err.shape, 1e-12) if binary64 else np.broadcast_to(binary32_gate(nterms, extra), err.shape)
+    over = err - tol
+    k = int(np.argmax(over))
+    assert over.flat[k] <= 0, "%s: normalised error %.3e > gate %.3e at output %s (max error %.3e)" % (
+        what, err.flat[k], tol.flat[k], np.unravel_index(k, err.shape), err.max())
+    return float(err.max())
+
+
+def row_lengths(pos):
+    """Entries of every row (or fiber) of a Compressed level."""
+    return np.diff(np.asarray(pos, dtype=np.int64))

@@ -199,3 +199,32 @@ def test_host_tensors_are_refused():
         spd.CSR(pos, crd, vals, (2, 2))
     with pytest.raises(TypeError, match="no CPU path"):
         spd.CSF3(pos, crd, pos, crd, vals, (2, 2, 2))
+
+
+def noalloc_item_limit(lib):
+    """Largest nrows + nnz whose nnz-split SpMV workspace fits the 1 MiB array of
+    spd_spmv_noalloc (from the size query, by bisection)."""
+    def ws(items):
+        d = _abi.spd_csr(1, 1, items - 1, 256, 512, 1024, _abi.SPD_F32, 0)
+        b = ctypes.c_size_t(0)
+        assert lib.spd_csr_workspace_size(0, ctypes.byref(d), 1, 0, None, ctypes.byref(b)) == 0
+        return b.value
+
+    lo, hi = 1, (1 << 31) - 2
+    while hi - lo > 1:
+        mid = (lo + hi) // 2
+        lo, hi = (mid, hi) if ws(mid) <= (1 << 20) else (lo, mid)
+    assert ws(lo) <= (1 << 20) < ws(lo + 1)
+    return lo
+
+
+def test_noalloc_scratch_limit():
+    """spd_spmv_noalloc rejects, on the host and before any launch, the first size whose
+    workspace exceeds its 1 MiB array (the GPU test runs the largest accepted size)."""
+    lib = _abi.load()
+    assert lib.spd_checked() == 0
+    lo = noalloc_item_limit(lib)
+    assert lo > 100_000_000  # the header's "about 107 million"
+    d = _abi.spd_csr(1, 1, lo, 256, 512, 1024, _abi.SPD_F32, 0)  # nrows + nnz = lo + 1
+    assert lib.spd_spmv_noalloc(ctypes.byref(d), 4096, _abi.SPD_F32, 8192, _abi.SPD_F32, None) == _abi.SPD_ERR_SHAPE
+    assert b"scratch" in lib.spd_last_error()

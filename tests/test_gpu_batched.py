@@ -12,11 +12,10 @@ import torch
 import oracle
 import spd_synth
 import paper_2207_13901_gb300 as spd
-from tests._util import normalized_error
+from tests._util import check_error, row_lengths
 
 pytestmark = pytest.mark.gpu
 
-TOL = {torch.float64: 1e-12, torch.float32: 1e-4, torch.bfloat16: 1e-4}
 
 
 def rounded(a, dtype):
@@ -42,8 +41,8 @@ def check_batch(mats, Xs, Ys, dtype):
         vr, Xr = rounded(A.vals, dtype), rounded(X, dtype)
         ref = oracle.spmm(A.pos, A.crd, vr, Xr, accurate=True)
         scale = oracle.spmm(A.pos, A.crd, np.abs(vr), np.abs(Xr))
-        err = normalized_error(Y.double().cpu().numpy(), ref, scale)
-        assert err.size == 0 or err.max() <= TOL[dtype], "matrix %d: %.3e" % (m, err.max())
+        check_error(Y.double().cpu().numpy(), ref, scale, dtype == torch.float64, row_lengths(A.pos)[:, None],
+                    "matrix %d" % m)
 
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16, torch.float64])

@@ -9,7 +9,8 @@ import torch
 import oracle
 import spd_synth
 import paper_2207_13901_gb300 as spd
-from tests.test_gpu_kernels import DTYPES, TOL, check, dev, dev_csr, get_mats, rounded
+from tests._util import row_lengths
+from tests.test_gpu_kernels import DTYPES, check, dev, dev_csr, get_mats, rounded
 
 pytestmark = pytest.mark.gpu
 
@@ -52,7 +53,9 @@ def test_spmm_accumulate(name, dtype):
         Y = torch.as_tensor(Y0).to(rdt).cuda()
         spd.spmm_accumulate(dA, dev(X, dtype), Y, split=split)
         torch.cuda.synchronize()
-        check(Y.double().cpu().numpy(), ref, scale, dtype, "spmm_accumulate %s %s %s" % (name, dtype, split))
+        # Y0 adds one term to every output
+        check(Y.double().cpu().numpy(), ref, scale, dtype, "spmm_accumulate %s %s %s" % (name, dtype, split),
+              row_lengths(A.pos)[:, None] + 1)
 
 
 @pytest.mark.parametrize("name", ["rmat12", "longrow", "banded", "no_nnz"])
@@ -69,4 +72,5 @@ def test_spmm_column_blocked(name, dtype, L):
     for nblk in (1, 4, 16):
         Y = spd.spmm_column_blocked(dA, dev(X, dtype), nblk=nblk)
         torch.cuda.synchronize()
-        check(Y.double().cpu().numpy(), ref, scale, dtype, "column blocked %s %s L=%d nblk=%d" % (name, dtype, L, nblk))
+        check(Y.double().cpu().numpy(), ref, scale, dtype, "column blocked %s %s L=%d nblk=%d" % (name, dtype, L, nblk),
+              row_lengths(A.pos)[:, None])
