@@ -2,7 +2,10 @@
 // CSF tensor B = {Dense, Compressed, Compressed}.
 //
 // Every entry (i,j,k) contributes (B(i,j,k) * C(j,:)) * D(k,:) to row i of A, formed in
-// the order the statement is written. One warp consumes one piece of entries; entries
+// the order the statement is written. In the binary32 modes a slice with more than 4096
+// entries is accumulated with Kahan's compensated summation: each warp step's U entries
+// are summed into a short local partial, and that partial is added to the slice's running
+// sum with a compensation term (kept in shared memory). One warp consumes one piece of entries; entries
 // come in windows of 32 whose fiber (hence j) and slice (i) each lane finds with a
 // lane-parallel search over 32-entry windows of pos2 and pos1. Lanes form groups of G
 // (G * EPL covers R), so a warp step covers 32/G entries; the groups' partial rows are
@@ -22,6 +25,8 @@
 #include "spd_internal.cuh"
 
 namespace spd {
+
+constexpr int32_t kLongSlice = 4096;  // slices with more entries are accumulated with compensation
 
 // s_c for every interior piece boundary: the number of slices whose end (pos1[i+1])
 // is at or before the piece's first fiber. Binary search over pos1[1..I].
@@ -47,8 +52,10 @@ __global__ void slice_partition_kernel(int64_t I, const int32_t *__restrict__ po
     pslice[c] = (int32_t)lo;
 }
 
+// 4 resident blocks of 256 threads (64 registers): measured faster than 3 blocks with
+// the compensation kept spill-free (73 registers).
 template <typename VT, int EPL, int G>
-__global__ void __launch_bounds__(256) spmttkrp_warp_kernel(
+__global__ void __launch_bounds__(256, 4) spmttkrp_warp_kernel(
     int64_t I, int64_t F, const int32_t *__restrict__ pos1, const int32_t *__restrict__ crd1,
     const int32_t *__restrict__ pos2, const int32_t *__restrict__ crd2, const VT *__restrict__ vals,
     const VT *__restrict__ C, uint32_t ldc_b, const VT *__restrict__ D, uint32_t ldd_b, int64_t R,
@@ -61,6 +68,7 @@ __global__ void __launch_bounds__(256) spmttkrp_warp_kernel(
     constexpr int U = 4;  // warp steps in flight
     __shared__ int32_t s_j_all[8][32], s_k_all[8][32], s_sl_all[8][32];
     __shared__ AT s_v_all[8][32];
+    __shared__ AT s_cmp_all[8][EPL * 32];  // Kahan compensations of a long slice, element e at [e * 32 + lane]
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
     const int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid;
@@ -90,18 +98,32 @@ __global__ void __launch_bounds__(256) spmttkrp_warp_kernel(
     (void)f1;
     int32_t *s_j = s_j_all[wid], *s_k = s_k_all[wid], *s_sl = s_sl_all[wid];
     AT *s_v = s_v_all[wid];
+    AT *cmp = s_cmp_all[wid] + lane;  // compensation of element e at cmp[32 * e]
 
     AT acc[EPL];
 #pragma unroll
     for (int e = 0; e < EPL; ++e) acc[e] = 0;
     bool dirty = false;  // acc holds contributions
     int32_t cs = s0;     // slice being accumulated (the same in every lane)
+    // whether slice s holds more than kLongSlice entries (binary32 accumulation only);
+    // the same four loads in every lane of the warp
+    constexpr bool kComp = sizeof(AT) == 4;  // binary64 sums need no compensation
+    auto long_slice = [&](int32_t s) {
+        if (!kComp || s >= I) return false;
+        return __ldg(pos2 + __ldg(pos1 + s + 1)) - __ldg(pos2 + __ldg(pos1 + s)) > kLongSlice;
+    };
+    bool ka = long_slice(cs);  // compensated accumulation of slice cs
+    auto clear_cmp = [&]() {
+#pragma unroll
+        for (int e = 0; e < EPL; ++e) cmp[32 * e] = (AT)0;
+    };
+    if (kComp && ka) clear_cmp();
 
     // total of acc over the groups of the warp (every lane ends with it)
     auto warp_total = [&](AT (&t)[EPL]) {
 #pragma unroll
         for (int e = 0; e < EPL; ++e) {
-            t[e] = acc[e];
+            t[e] = kComp && ka ? acc[e] - cmp[32 * e] : acc[e];
 #pragma unroll
             for (int off = G; off < 32; off <<= 1) t[e] += __shfl_xor_sync(0xffffffffu, t[e], off);
         }
@@ -124,6 +146,8 @@ __global__ void __launch_bounds__(256) spmttkrp_warp_kernel(
         for (int e = 0; e < EPL; ++e) acc[e] = 0;
         dirty = false;
         cs = next;
+        ka = long_slice(cs);
+        if (kComp && ka) clear_cmp();
     };
 
     PosRows fw, sw;  // fiber ends (in entries) and slice ends (in fibers)
@@ -184,10 +208,25 @@ __global__ void __launch_bounds__(256) spmttkrp_warp_kernel(
                         }
                     }
                 }
+                if (!kComp || !ka) {
 #pragma unroll
-                for (int u = 0; u < U; ++u) {
+                    for (int u = 0; u < U; ++u) {
 #pragma unroll
-                    for (int e = 0; e < EPL; ++e) acc[e] = fma(v[u] * (AT)cv[u].at(e), (AT)dv[u].at(e), acc[e]);
+                        for (int e = 0; e < EPL; ++e) acc[e] = fma(v[u] * (AT)cv[u].at(e), (AT)dv[u].at(e), acc[e]);
+                    }
+                } else {
+                    // the step's U entries summed locally, then added to the running sum with
+                    // Kahan's compensation
+#pragma unroll
+                    for (int e = 0; e < EPL; ++e) {
+                        AT loc = (AT)0;
+#pragma unroll
+                        for (int u = 0; u < U; ++u) loc = fma(v[u] * (AT)cv[u].at(e), (AT)dv[u].at(e), loc);
+                        const AT y = loc - cmp[32 * e];
+                        const AT t = acc[e] + y;
+                        cmp[32 * e] = (t - acc[e]) - y;
+                        acc[e] = t;
+                    }
                 }
             }
             dirty = true;

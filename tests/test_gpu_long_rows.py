@@ -174,3 +174,22 @@ def test_spttv_long_fiber(dtype):
         out = spd.spttv(dT, dev(c, dtype), split=split)
         check_error(out.double().cpu().numpy(), ref, scale, dtype == torch.float64, row_lengths(T.pos2),
                     "spttv long fiber %s %s" % (dtype, split))
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("R", [16, 32, 64])
+def test_spmttkrp_long_slice(dtype, R):
+    T = long_slice_tensor(dtype)
+    v, xv = DATA[dtype]
+    rng = np.random.default_rng(6)
+    C = rng.uniform(-1, 1, (T.dims[1], R))
+    C[:1541] = 1.0  # the long slice's fibers meet rows of ones, so every term is v * xv
+    D = np.full((T.dims[2], R), xv)
+    vr, Cr, Dr = rounded(T.vals, dtype), rounded(C, dtype), rounded(D, dtype)
+    assert_adversarial(np.full(LONG, rounded([v], dtype)[0] * rounded([xv], dtype)[0]))
+    ref = oracle.spmttkrp(T.pos1, T.crd1, T.pos2, T.crd2, vr, Cr, Dr, accurate=True)
+    scale = oracle.spmttkrp(T.pos1, T.crd1, T.pos2, T.crd2, np.abs(vr), np.abs(Cr), np.abs(Dr))
+    slice_len = row_lengths(np.asarray(T.pos2, dtype=np.int64)[np.asarray(T.pos1, dtype=np.int64)])
+    dT = spd.CSF3.from_host(T.pos1, T.crd1, T.pos2, T.crd2, T.vals, T.dims, dtype=dtype)
+    for split, tune in [("nnz", None), ("nnz", {"unit_items": 512}), ("row", None)]:
+        A = spd.spmttkrp(dT, dev(C, dtype), dev(D, dtype), split=split, tune=tune)
+        check_error(A.double().cpu().numpy(), ref, scale, dtype == torch.float64, slice_len[:, None],
+                    "spmttkrp long slice %s R=%d %s %s" % (dtype, R, split, tune), extra=1)
