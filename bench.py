@@ -57,6 +57,8 @@ def parse_args(argv=None):
     p.add_argument("--rows", default="all",
                    help="comma list of extra hot-path rows to measure: cfg1,sddmm,backward,csf,batched,banded,spadd3,colblock "
                         "(or all, none)")
+    p.add_argument("--record-traffic", nargs=5, metavar=("CSV", "KERNEL", "CASE", "TUNE", "COMMAND"),
+                   help="store the counters of an ncu raw CSV export in profiles/traffic.json and exit")
     p.add_argument("--case", default="",
                    help="time one kernel case alone and exit (for profiling): sddmm:K:DTYPE on the 2^20-row R-MAT "
                         "with 32 samples per row, or spmttkrp:R:DTYPE on the Zipf CSF tensor (DTYPE f32, bf16 or "
@@ -136,39 +138,79 @@ def algorithmic_bytes(kernel: str, n: int, nnz: int, vbytes: int, xbytes: int, y
     return base + xbytes * n * L + ybytes * n * L
 
 
-SPMM_SOURCES = ("paper_2207_13901_gb300/csrc/spd_spmm.cu", "paper_2207_13901_gb300/csrc/spd_spmm_piece.cuh",
-                "paper_2207_13901_gb300/csrc/spd_internal.cuh", "paper_2207_13901_gb300/csrc/spd_core.cu")
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_spmm_rmat22_f32.md")
+# Sources each kernel's recorded ncu counters depend on: a record is used only while
+# these files are unchanged (their hash is stored with it).
+KERNEL_SOURCES = {
+    "spmm": ("spd_spmm.cu", "spd_spmm_piece.cuh"),
+    "spmv": ("spd_spmv.cu",),
+    "spttv": ("spd_spmv.cu",),
+    "sddmm": ("spd_sddmm.cu",),
+    "spmttkrp": ("spd_mttkrp.cu",),
+}
+COMMON_SOURCES = ("spd_internal.cuh", "spd_core.cu")
+TRAFFIC_JSON = os.path.join(ROOT, "profiles", "traffic.json")
 
 
-def spmm_source_hash() -> str:
+def source_hash(kernel: str) -> str:
     import hashlib
     h = hashlib.sha256()
-    for rel in SPMM_SOURCES:
-        with open(os.path.join(ROOT, rel), "rb") as f:
+    for rel in KERNEL_SOURCES[kernel] + COMMON_SOURCES:
+        with open(os.path.join(ROOT, "paper_2207_13901_gb300", "csrc", rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(tune, scale):
-    """DRAM bytes per SpMM call from the committed ncu summary, if it was taken on the
-    same R-MAT scale, the current kernel sources and the same tuning; otherwise None."""
-    if not os.path.exists(TRAFFIC_FILE):
-        return None
-    vals = {}
-    with open(TRAFFIC_FILE) as f:
-        for line in f:
-            if ":" in line and line.strip().startswith("- "):
-                k, v = line.strip()[2:].split(":", 1)
-                vals[k.strip()] = v.strip().strip("`")
+def recorded_traffic(kernel: str, case: str, tune: str, path: str = TRAFFIC_JSON):
+    """ncu counters of one launch of `kernel` on `case` (DRAM bytes read + written, L2 hit
+    rate) from the committed record, if it was taken on the current kernel sources and the
+    same tuning; otherwise None."""
     try:
-        if int(vals["scale"]) != scale or vals.get("source_hash") != spmm_source_hash():
-            return None
-        if vals.get("tune") != "%d,%d,%d" % (tune["unit_items"], tune["block_threads"], tune.get("inflight", 8)):
-            return None
-        return int(vals["dram_bytes_per_spmm_call"])
-    except (KeyError, ValueError, TypeError):
+        with open(path) as f:
+            rec = json.load(f).get("records", {}).get(kernel + "|" + case)
+    except (OSError, ValueError):
         return None
+    if not rec or rec.get("source_hash") != source_hash(kernel) or rec.get("tune") != tune:
+        return None
+    return {"dram_bytes": int(rec["dram_bytes"]), "l2_hit_pct": rec.get("l2_hit_pct"), "kernel_name": rec.get("kernel_name")}
+
+
+def tune_key(tune) -> str:
+    """Tuning of a recorded launch: unit items, threads per block, rows in flight."""
+    t = tune or {}
+    return "%d,%d,%d" % (t.get("unit_items", 0), t.get("block_threads", 0), t.get("inflight", 0))
+
+
+def record_traffic(csv_path: str, kernel: str, case: str, tune: str, command: str, path: str = TRAFFIC_JSON) -> dict:
+    """Stores the counters of the last launch in an ncu raw CSV export (``ncu -i REPORT
+    --page raw --csv``): dram__bytes_read.sum + dram__bytes_write.sum and
+    lts__t_sector_hit_rate.pct, with the hash of the kernel's sources and the tuning."""
+    import csv
+    with open(csv_path) as f:
+        rows = [r for r in csv.reader(f)]
+    hdr, units, last = rows[0], rows[1], rows[-1]
+    col = {h: i for i, h in enumerate(hdr)}
+
+    def val(name):
+        v = float(last[col[name]].replace(",", ""))
+        u = units[col[name]]
+        return v * {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}.get(u, 1)
+
+    rec = {"kernel_name": last[col["Kernel Name"]] if "Kernel Name" in col else "",
+           "dram_bytes": int(val("dram__bytes_read.sum") + val("dram__bytes_write.sum")),
+           "l2_hit_pct": round(val("lts__t_sector_hit_rate.pct"), 2),
+           "duration_us_under_ncu": round(val("gpu__time_duration.sum") / (1e3 if units[col["gpu__time_duration.sum"]] == "nsecond" else 1), 2),
+           "tune": tune, "source_hash": source_hash(kernel), "command": command}
+    try:
+        with open(path) as f:
+            data = json.load(f)
+    except (OSError, ValueError):
+        data = {}
+    data.setdefault("records", {})[kernel + "|" + case] = rec
+    data["about"] = ("ncu counters of one launch of each kernel on its workload (one kernel, one launch, "
+                     "--clock-control none); bench.py reports them while the kernel's sources are unchanged")
+    with open(path, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    return rec
 
 
 def measured_peaks():
@@ -387,6 +429,8 @@ def run_gpu(args):
     spmm_bytes = algorithmic_bytes("spmm", n, nnz, 4, 4, 4)
     spmv_bytes = algorithmic_bytes("spmv", n, nnz, 4, 4, 4)
     spmm_gbs = spmm_bytes / (spmm_ms * 1e-3) / 1e9
+    spmm_rec = (recorded_traffic("spmm", "rmat%d_f32_L%d" % (args.scale, L_COLS), tune_key(tu_m))
+                if sp_m == "nnz" else None)
 
     # ---------------- errors of the measured step (sampled rows vs the compensated oracle)
     rng = np.random.default_rng(0)
@@ -600,9 +644,10 @@ def run_gpu(args):
                 "peak_kind": peak_kind,
                 "unit": "GB/s",
                 "frac": round(spmm_gbs / hbm, 4),
-                "traffic": recorded_traffic(tu_m, args.scale) if (sp_m == "nnz" and tu_m) else None,
-                "traffic_source": "profiles/traffic_spmm_rmat22_f32.md (ncu dram__bytes_read.sum + dram__bytes_write.sum "
-                                  "of the partition, warp and fix-up kernels of one call)",
+                "traffic": (spmm_rec or {}).get("dram_bytes"),
+                "l2_hit_pct": (spmm_rec or {}).get("l2_hit_pct"),
+                "traffic_source": "profiles/traffic.json (ncu dram__bytes_read.sum + dram__bytes_write.sum and "
+                                  "lts__t_sector_hit_rate.pct of one spmm_warp_kernel launch on this workload)",
                 "algorithmic_bytes": spmm_bytes,
                 "spmv_achieved": round(spmv_bytes / (spmv_ms * 1e-3) / 1e9, 1),
                 "spmv_frac": round(spmv_bytes / (spmv_ms * 1e-3) / 1e9 / hbm, 4),
@@ -1140,7 +1185,10 @@ def run_reference(args):
 
 def main(argv=None):
     args = parse_args(argv)
-    if args.impl == "reference":
+    if args.record_traffic:
+        csv_path, kernel, case, tune, command = args.record_traffic
+        print(json.dumps(record_traffic(csv_path, kernel, case, tune, command)))
+    elif args.impl == "reference":
         run_reference(args)
     elif args.case:
         run_case(args)

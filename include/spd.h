@@ -62,7 +62,7 @@
 extern "C" {
 #endif
 
-#define SPD_ABI_VERSION 1
+#define SPD_ABI_VERSION 2
 
 typedef enum {
     SPD_OK = 0,
@@ -131,13 +131,20 @@ typedef struct {
  *                 4, 8 or 16 lanes, one 16-byte vector each, taking different nonzeros
  *                 side by side; 2 = one nonzero per warp step over 32 narrower lanes;
  *                 0 = the library's choice (groups when X is at most 64 MiB, so that its
- *                 rows stay in L2 and the gathers are bound by instruction issue). */
+ *                 rows stay in L2 and the gathers are bound by instruction issue).
+ *   spmv_form     kernel form of SpMV and SpTTV: 1 = a thread block per piece with
+ *                 tiles of 2048 items (little shared memory, so L1 keeps caching the
+ *                 gathered x: the better form for power-law columns); 2 = a warp per
+ *                 piece with tiles of 256 items whose crd/vals windows arrive by bulk
+ *                 copies (TMA) one tile ahead (the better form when x is read locally,
+ *                 e.g. banded matrices); 0 = the library's choice (currently 1). */
 typedef struct {
     int32_t unit_items;
     int32_t row_pieces;
     int32_t block_threads;
     int32_t inflight;
     int32_t lane_groups;
+    int32_t spmv_form;
 } spd_tune;
 
 /* -------------------------------------------------------------------- misc */
@@ -168,6 +175,13 @@ spd_status spd_set_checked(int on);
 
 /* 1 while checked mode is on, else 0. */
 int spd_checked(void);
+
+/* Device faults of earlier calls: kernels that stage data with bulk copies wait for them
+ * with a bounded wait (1 s); one that gives up records bit 1 in a device fault word and
+ * leaves its outputs unspecified. This call synchronizes `stream`, stores the OR of the
+ * recorded bits in *flags (0 when none), clears them, and returns SPD_ERR_TIMEOUT when any
+ * was set. Checked mode performs the same check after every call. Not during a capture. */
+spd_status spd_fault_status(uint32_t *flags, void *stream);
 
 /* -------------------------------------------------------------------- sizes */
 

@@ -47,6 +47,7 @@ class spd_tune(ctypes.Structure):
     _fields_ = [
         ("unit_items", ctypes.c_int32), ("row_pieces", ctypes.c_int32),
         ("block_threads", ctypes.c_int32), ("inflight", ctypes.c_int32), ("lane_groups", ctypes.c_int32),
+        ("spmv_form", ctypes.c_int32),
     ]
 
 
@@ -84,6 +85,7 @@ SIGNATURES = {
     "spd_last_error": (ctypes.c_char_p, []),
     "spd_set_checked": (_I, [_I]),
     "spd_checked": (ctypes.c_int, []),
+    "spd_fault_status": (_I, [ctypes.POINTER(ctypes.c_uint32), _P]),
     "spd_csr_workspace_size": (_I, [_I, _CSR, _I, _I64, _TUNE, ctypes.POINTER(ctypes.c_size_t)]),
     "spd_csf3_workspace_size": (_I, [_I, _CSF, _I, _I64, _TUNE, ctypes.POINTER(ctypes.c_size_t)]),
     "spd_csr_validate": (_I, [_CSR, _P, _SZ, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64), _P]),
@@ -136,7 +138,7 @@ def load(build_if_needed: bool = True):
             fn = getattr(lib, name)
             fn.restype = res
             fn.argtypes = args
-        if lib.spd_abi_version() != 1:
+        if lib.spd_abi_version() != 2:
             raise RuntimeError("libspd ABI version mismatch")
         _lib = lib
         return lib

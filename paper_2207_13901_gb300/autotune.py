@@ -2,7 +2,7 @@
 
 For a shape class -- (operation, element type, log2 buckets of rows, nonzeros and the
 longest row, dense width, device name) -- every candidate setting (row vs nnz split,
-items per work unit, threads per block, rows in flight, SpMM lane shape) is timed with CUDA events on the
+items per work unit, threads per block, rows in flight, SpMM lane shape, SpMV kernel form) is timed with CUDA events on the
 caller's operands, and the fastest is kept in a JSON cache (``SPD_AUTOTUNE_CACHE``, by
 default ``~/.cache/spd/autotune.json``). Timing runs the real kernels through the C ABI
 outside any timed region of the caller; it reads the longest row once with a device
@@ -47,7 +47,8 @@ def warp_candidates(include_row: bool = True, inflight: bool = True) -> List[dic
 
 
 def spmv_candidates() -> List[dict]:
-    return [{"split": "nnz", "tune": None}, {"split": "row", "tune": None}]
+    """Both splits with both kernel forms of SpMV (block tiles, warp tiles with bulk copies)."""
+    return [{"split": split, "tune": {"spmv_form": form}} for split in ("nnz", "row") for form in (1, 2)]
 
 
 class Autotuner:
@@ -129,7 +130,8 @@ class Autotuner:
     def spmv(self, A: "ops.CSR", x: torch.Tensor, y: Optional[torch.Tensor] = None, force: bool = False) -> dict:
         y = y if y is not None else torch.empty(A.shape[0], dtype=ops.result_dtype(A.dtype), device=x.device)
         key = self.shape_key("spmv", A, 1, A.dtype)
-        return self.choose(key, spmv_candidates(), lambda c: (lambda: ops.spmv(A, x, y, split=c["split"])), force)
+        return self.choose(key, spmv_candidates(),
+                           lambda c: (lambda: ops.spmv(A, x, y, split=c["split"], tune=c["tune"])), force)
 
     def sddmm(self, B: "ops.CSR", C: torch.Tensor, Dnk: torch.Tensor, force: bool = False) -> dict:
         out = torch.empty(B.nnz, dtype=ops.result_dtype(C.dtype), device=C.device)

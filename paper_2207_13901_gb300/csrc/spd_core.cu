@@ -70,6 +70,7 @@ spd_status read_tune(const spd_tune *t, Tuning *out) {
     out->block_threads = kWarpBlockDefault;
     out->inflight = 8;
     out->lane_groups = 0;
+    out->spmv_form = 0;
     if (!t) return SPD_OK;
     if (t->unit_items) {
         if (t->unit_items < 32 || t->unit_items > 65536 || t->unit_items % 32)
@@ -92,6 +93,8 @@ spd_status read_tune(const spd_tune *t, Tuning *out) {
     }
     if (t->lane_groups < 0 || t->lane_groups > 2) return fail(SPD_ERR_ARG, "lane_groups %d not in 0..2", t->lane_groups);
     out->lane_groups = t->lane_groups;
+    if (t->spmv_form < 0 || t->spmv_form > 2) return fail(SPD_ERR_ARG, "spmv_form %d not in 0..2", t->spmv_form);
+    out->spmv_form = t->spmv_form;
     return SPD_OK;
 }
 
@@ -382,6 +385,10 @@ spd_status checked_finish(spd_status s, const char *call, cudaStream_t st) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return fail(SPD_ERR_CUDA, "%s: %s", call, cudaGetErrorString(e));
+    unsigned int faults = 0;
+    spd_status f = take_device_faults(&faults);
+    if (f) return f;
+    if (faults) return fail(SPD_ERR_TIMEOUT, "%s: a bounded device wait gave up (flags 0x%x)", call, faults);
     return SPD_OK;
 }
 

@@ -195,6 +195,69 @@ __device__ __forceinline__ void comp_add(T &hi, T &lo, T b) {
     hi = s;
 }
 
+// ------------------------------------------------------------------ bulk copies (TMA)
+
+// A kernel whose bounded wait gives up ORs a kFault* bit into the device fault word of its
+// translation unit and returns early (its results are then unspecified); spd_fault_status
+// reads and clears the words.
+constexpr unsigned kFaultBulkWait = 1u;  // a bulk copy did not complete within kWaitLimitNs
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // 1 s
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// One-arrival mbarrier for the completion of bulk copies (PTX ISA, "mbarrier").
+__device__ __forceinline__ void mbar_init(uint64_t *bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+}
+// Makes initialized mbarriers visible to the asynchronous (bulk copy) proxy.
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+// The single arrival of a phase, announcing `bytes` of bulk copies that complete it.
+__device__ __forceinline__ void mbar_arrive_expect(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Waits until the phase of `bar` with the given parity has completed, for at most
+// kWaitLimitNs; false (and kFaultBulkWait set in *fault) when the limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned int *fault) {
+    if (mbar_test(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_test(bar, parity)) {
+        if (global_ns() - t0 > kWaitLimitNs) {
+            atomicOr(fault, kFaultBulkWait);
+            return false;
+        }
+    }
+    return true;
+}
+// Orders this thread's earlier generic-proxy accesses of shared memory before later
+// bulk copies into it.
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// 1-D bulk copy (TMA) of `bytes` from global to shared memory, completing on `bar`.
+// Both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
 // ------------------------------------------------------------------ partitions
 
 // Merge-path state of the flattened coordinate tree: after d items, `rows` rows have
@@ -332,6 +395,9 @@ bool checked_mode();
 spd_status checked_csr(const spd_csr *A, const char *name, cudaStream_t st);
 spd_status checked_csf3(const spd_csf3 *B, const char *name, cudaStream_t st);
 spd_status checked_finish(spd_status s, const char *call, cudaStream_t st);
+// Reads and clears the device fault words of the kernels with bounded waits (OR of the
+// kFault* bits); synchronous, not for use during a graph capture.
+spd_status take_device_faults(unsigned int *flags);
 
 // Defaults shared by the size queries and the compute calls.
 constexpr int kSpmvThreads = 256;   // threads of the tile-per-block SpMV / SpTTV kernel
@@ -346,6 +412,7 @@ struct Tuning {
     int block_threads;    // threads per block (warp kernels)
     int inflight;         // dense rows in flight per group (SpMM)
     int lane_groups;      // SpMM lane shape: 0 = by the size of X, 1 = groups, 2 = 32 lanes
+    int spmv_form;        // SpMV / SpTTV kernel form: 0 = library's choice, 1 = block tiles, 2 = warp tiles
 };
 spd_status read_tune(const spd_tune *t, Tuning *out);
 int resolve_split(int split);

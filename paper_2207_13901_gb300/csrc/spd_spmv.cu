@@ -22,6 +22,21 @@
 
 namespace spd {
 
+constexpr int kSpmvWarpIPT = 8;  // items per lane of a warp tile
+
+// Fault word of the kernels in this file (see kFaultBulkWait).
+static __device__ unsigned int g_spmv_fault;
+
+spd_status take_device_faults(unsigned int *flags) {
+    unsigned int h = 0;
+    const unsigned int zero = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(&h, g_spmv_fault, sizeof(h));
+    if (e == cudaSuccess && h) e = cudaMemcpyToSymbol(g_spmv_fault, &zero, sizeof(zero));
+    if (e != cudaSuccess) return fail(SPD_ERR_CUDA, "fault word: %s", cudaGetErrorString(e));
+    *flags = h;
+    return SPD_OK;
+}
+
 // Shared-memory index with one padding word per 32 entries: each thread consumes IPT
 // consecutive entries, so without the skew a warp's 32 threads would fall on only
 // 32/IPT banks.
@@ -213,6 +228,302 @@ __global__ void __launch_bounds__(NT, sizeof(VT) == 2 ? 8 : 6) spmv_tile_kernel(
     }
 }
 
+// ------------------------------------------------------------------ warp-tile form
+//
+// One warp consumes one piece, tile by tile (T = 32 * IPT items), with no block-wide
+// barrier:
+//   * the row ends of the tile set bits in a per-warp bitmap (the ends of the next 64
+//     rows are fetched one tile ahead, two per lane; a run of more row ends is loaded
+//     together); a warp scan of the popcounts of each lane's IPT bits places every lane
+//     on its first row;
+//   * the tile's window of crd (the next T coordinates) arrives in shared memory by a
+//     1-D bulk copy (TMA) issued one tile ahead into a double buffer and completing on an
+//     mbarrier per buffer (bounded wait); vals are streamed with plain coalesced loads
+//     issued together with the gathers of x, so one latency covers both;
+//   * the products vals * x[crd] go to a skewed per-warp array; each lane sums its IPT
+//     items in order without branches; a segmented warp scan hands each lane the
+//     partial of the row it started in, and the open row is carried into the next tile
+//     with compensated addition.
+// crd not 16-byte aligned takes plain coalesced loads into the same buffers.
+template <typename VT, int IPT>
+struct WarpSpmvLayout {
+    using AT = typename Traits<VT>::acc;
+    static constexpr int T = 32 * IPT;
+    static constexpr int BUF = T + 16;  // staged elements: the window plus its 16-byte alignment slack
+    static constexpr size_t off_bar = 0;                                    // 2 mbarriers
+    static constexpr size_t off_bits = 16;                                  // IPT words
+    static constexpr size_t off_crd = (off_bits + 4 * IPT + 15) / 16 * 16;  // [2][BUF] int32
+    static constexpr size_t off_val = off_crd + 2 * BUF * 4;                // [2][BUF] VT
+    static constexpr size_t off_prod = (off_val + 2 * BUF * sizeof(VT) + 15) / 16 * 16;  // [T + T/32] AT
+    static constexpr size_t bytes = (off_prod + (T + T / 32) * sizeof(AT) + 15) / 16 * 16;  // per warp
+};
+
+template <typename VT, int IPT, bool BULK>
+__global__ void __launch_bounds__(256) spmv_warp_kernel(
+    int64_t n, int64_t nnz, const int32_t *__restrict__ pos, const int32_t *__restrict__ crd,
+    const VT *__restrict__ vals, const VT *__restrict__ x, typename Traits<VT>::out *__restrict__ y,
+    const int32_t *__restrict__ prow, const int32_t *__restrict__ ppos, int64_t npieces,  // nnz split
+    int64_t P, int64_t nouter, const int32_t *__restrict__ outer,                         // row split
+    int32_t *__restrict__ carry_row, double *__restrict__ carry_val) {
+    using AT = typename Traits<VT>::acc;
+    using OT = typename Traits<VT>::out;
+    using Lay = WarpSpmvLayout<VT, IPT>;
+    constexpr int T = Lay::T;
+    constexpr int LPW = 32 / IPT;  // lanes per bitmap word
+    constexpr unsigned FULL = 0xffffffffu;
+    constexpr uint32_t MASK = IPT == 32 ? FULL : ((1u << IPT) - 1u);
+    static_assert(32 % IPT == 0 && IPT >= 2, "a lane's items share one bitmap word");
+    extern __shared__ __align__(16) unsigned char spmv_smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid;
+    if (c >= (prow ? npieces : P)) return;  // whole warp
+    unsigned char *ws = spmv_smem + (size_t)wid * Lay::bytes;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(ws + Lay::off_bar);
+    uint32_t *bits = reinterpret_cast<uint32_t *>(ws + Lay::off_bits);
+    int32_t *s_crd = reinterpret_cast<int32_t *>(ws + Lay::off_crd);
+    VT *s_val = reinterpret_cast<VT *>(ws + Lay::off_val);
+    AT *s_prod = reinterpret_cast<AT *>(ws + Lay::off_prod);
+    constexpr int EV = (int)(16 / sizeof(VT));  // values per 16 bytes
+
+    PieceBounds b;
+    if (prow) {
+        b = nnz_piece(c, prow, ppos);
+    } else if (outer) {  // SpTTV row split: slices [floor(c I/P), floor((c+1) I/P)) and their fibers
+        const int64_t i0 = (c * nouter) / P, i1 = ((c + 1) * nouter) / P;
+        b.r0 = __ldg(outer + i0);
+        b.r1 = __ldg(outer + i1);
+        b.p0 = __ldg(pos + b.r0);
+        b.p1 = __ldg(pos + b.r1);
+    } else {
+        b = row_piece(c, P, n, pos);
+    }
+
+    // bulk copies of crd and vals [ps, ps + T) (clamped to nnz) into buffer bi, by lane 0:
+    // each starts at the 16-byte boundary below ps and, at the array's end, stops at the
+    // last 16-byte boundary; the few elements after it are loaded by the lanes after the wait
+    auto span = [&](int32_t ps, int E, int64_t &a, int64_t &e, int64_t &end) {
+        end = (int64_t)ps + T < nnz ? (int64_t)ps + T : nnz;
+        a = ps & ~(int64_t)(E - 1);
+        e = (end + E - 1) & ~(int64_t)(E - 1);
+        if (e > nnz) e = end & ~(int64_t)(E - 1);
+        if (e < a) e = a;
+    };
+    auto issue = [&](int bi, int32_t ps) {
+        int64_t ac, ec, av, ev, end;
+        span(ps, 4, ac, ec, end);
+        span(ps, EV, av, ev, end);
+        const uint32_t cb = (uint32_t)((ec - ac) * 4), vb = (uint32_t)((ev - av) * sizeof(VT));
+        mbar_arrive_expect(&bar[bi], cb + vb);
+        if (cb) bulk_g2s(s_crd + bi * Lay::BUF, crd + ac, cb, &bar[bi]);
+        if (vb) bulk_g2s(s_val + bi * Lay::BUF, vals + av, vb, &bar[bi]);
+    };
+
+    int32_t r = b.r0, p = b.p0;
+    AT carry_hi = 0, carry_lo = 0;  // partial of row r accumulated over earlier tiles
+    int buf = 0;
+    uint32_t phase = 0;     // bit i: parity of the next completion of buffer i
+    uint32_t inflight = 0;  // bit i: a bulk copy into buffer i is outstanding
+    if (BULK) {
+        if (lane == 0) {
+            mbar_init(&bar[0]);
+            mbar_init(&bar[1]);
+            mbar_fence_init();
+        }
+        __syncwarp();
+        if ((int64_t)b.r1 - r + b.p1 - p > 0) {
+            if (lane == 0) issue(0, p);
+            inflight = 1u;
+        }
+    }
+    // ends of rows r .. r+63, two per lane (the next tile's are fetched one tile ahead)
+    int32_t rend0 = (int64_t)r + lane < n ? ld_stream(pos + r + 1 + lane) : INT_MAX;
+    int32_t rend1 = (int64_t)r + 32 + lane < n ? ld_stream(pos + r + 33 + lane) : INT_MAX;
+
+    while (true) {
+        const int64_t rem_rows = (int64_t)b.r1 - r, rem_nnz = (int64_t)b.p1 - p;
+        if (rem_rows + rem_nnz == 0) break;
+        const int items = (int)(rem_rows + rem_nnz < T ? rem_rows + rem_nnz : T);
+        const int nr = (int)(rem_rows < items ? rem_rows : items);  // rows that may end in the tile
+        if (lane < IPT) bits[lane] = 0u;
+        __syncwarp();
+        {
+            // item index of row r + q's end (rows past n read as INT_MAX: saturate)
+            auto item_of = [&](int32_t end_pos, int q) {
+                const int64_t e = (int64_t)end_pos - p + q;
+                return e < items ? (int)e : INT_MAX;
+            };
+            int e = item_of(rend0, lane);
+            if (lane < nr && e < items) atomicOr(&bits[e >> 5], 1u << (e & 31));
+            e = item_of(rend1, 32 + lane);
+            if (32 + lane < nr && e < items) atomicOr(&bits[e >> 5], 1u << (e & 31));
+            if (nr > 64 && __shfl_sync(FULL, e, 31) < items) {
+                // more than 64 rows end in the tile (a run of short or empty rows): the
+                // remaining row ends, loaded together, 32 at a time per lane group
+                for (int q0 = 64; q0 < nr; q0 += 128) {
+                    int32_t me[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int q = q0 + 32 * k + lane;
+                        me[k] = q < nr ? ld_stream(pos + r + 1 + q) : INT_MAX;
+                    }
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int q = q0 + 32 * k + lane;
+                        e = q < nr ? item_of(me[k], q) : INT_MAX;
+                        if (e < items) atomicOr(&bits[e >> 5], 1u << (e & 31));
+                    }
+                    if (__shfl_sync(FULL, e, 31) >= items) break;
+                }
+            }
+        }
+        __syncwarp();
+        const uint32_t mine = (bits[lane / LPW] >> ((lane % LPW) * IPT)) & MASK;
+        int incl = __popc(mine);
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int t = __shfl_up_sync(FULL, incl, off);
+            if (lane >= off) incl += t;
+        }
+        const int i0 = incl - __popc(mine);          // row ends before this lane's first item
+        const int ic = __shfl_sync(FULL, incl, 31);  // row ends in the tile
+        const int jc = items - ic;                   // nonzeros in the tile
+        const int32_t rn = r + ic, pn = p + jc;
+        const bool more = (int64_t)b.r1 - rn + b.p1 - pn > 0;
+        rend0 = (int64_t)rn + lane < n ? ld_stream(pos + rn + 1 + lane) : INT_MAX;
+        rend1 = (int64_t)rn + 32 + lane < n ? ld_stream(pos + rn + 33 + lane) : INT_MAX;
+
+        // element p + q of the tile sits at wc[oc + q] / wv[ov + q]
+        const int32_t *wc = s_crd + buf * Lay::BUF;
+        const VT *wv = s_val + buf * Lay::BUF;
+        int oc = 0, ov = 0;
+        if (BULK) {
+            if (more) {  // the other buffer was last read before the previous tile's final __syncwarp
+                if (lane == 0) {
+                    fence_proxy_async();
+                    issue(buf ^ 1, pn);
+                }
+                inflight |= 1u << (buf ^ 1);
+            }
+            const bool ok = mbar_wait(&bar[buf], (phase >> buf) & 1u, &g_spmv_fault);
+            inflight &= ~(1u << buf);
+            phase ^= 1u << buf;
+            if (!__all_sync(FULL, ok)) {  // give up (fault word set); wait once more for our copies
+                if ((inflight >> (buf ^ 1)) & 1u) mbar_wait(&bar[buf ^ 1], (phase >> (buf ^ 1)) & 1u, &g_spmv_fault);
+                return;
+            }
+            int64_t ac, ec, av, ev, end;
+            span(p, 4, ac, ec, end);
+            span(p, EV, av, ev, end);
+            oc = (int)(p - ac);
+            ov = (int)(p - av);
+            // the last elements of the arrays that the bulk copies could not cover
+            if (lane < end - ec) s_crd[buf * Lay::BUF + (int)(ec - ac) + lane] = ld_stream(crd + ec + lane);
+            if (lane < end - ev) s_val[buf * Lay::BUF + (int)(ev - av) + lane] = vals[ev + lane];
+        } else {
+            int32_t *dc = s_crd + buf * Lay::BUF;
+            VT *dv = s_val + buf * Lay::BUF;
+#pragma unroll
+            for (int k = 0; k < IPT; ++k) {
+                const int q = lane + 32 * k;
+                if (q < jc) {
+                    dc[q] = ld_stream(crd + p + q);
+                    dv[q] = vals[p + q];
+                }
+            }
+        }
+        __syncwarp();
+        // products of the tile's nonzeros (coalesced reads of the window, gathered x,
+        // all of a lane's gathers issued before any is used)
+        {
+            AT xv[IPT];
+#pragma unroll
+            for (int k = 0; k < IPT; ++k) {
+                const int q = lane + 32 * k;
+                xv[k] = q < jc ? ld_gather(x + wc[oc + q]) : (AT)0;
+            }
+#pragma unroll
+            for (int k = 0; k < IPT; ++k) {
+                const int q = lane + 32 * k;
+                if (q < jc) s_prod[skew(q)] = to_acc(wv[ov + q]) * xv[k];
+            }
+        }
+        __syncwarp();
+        // this lane's IPT items of the tile, in order, without branches: a row end writes
+        // the running sum of the row (the first one of the lane is completed by the scan)
+        const int k0 = lane * IPT;
+        const uint32_t valid = k0 >= items ? 0u : (items - k0 >= IPT ? MASK : ((1u << (items - k0)) - 1u));
+        const uint32_t ends = mine & valid;
+        const int nz = __popc(valid & ~ends);  // nonzeros of this lane
+        const int j0 = k0 - i0;
+        AT acc = 0, first_val = 0;
+        int i = i0;
+        bool first = true;
+#pragma unroll
+        for (int k = 0; k < IPT; ++k) {
+            const bool isend = (ends >> k) & 1u;
+            const bool isnz = ((valid & ~ends) >> k) & 1u;
+            const int jj = j0 + k - (i - i0);  // nonzero index of item k when it is one
+            const AT pv = isnz ? s_prod[skew(jj)] : (AT)0;
+            acc += pv;
+            if (isend) {
+                if (first) first_val = acc;
+                else y[r + i] = (OT)acc;
+                first = false;
+                acc = 0;
+                ++i;
+            }
+        }
+        (void)nz;
+        const int first_row = first ? -1 : i0;
+        // segmented inclusive scan of (ended a row, tail partial) over the warp
+        int f = first_row >= 0;
+        AT v = acc;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int pf = __shfl_up_sync(FULL, f, off);
+            const AT pv = __shfl_up_sync(FULL, v, off);
+            if (lane >= off) {
+                if (!f) v += pv;
+                f |= pf;
+            }
+        }
+        AT ev = __shfl_up_sync(FULL, v, 1);
+        int ef = __shfl_up_sync(FULL, f, 1);
+        if (lane == 0) {
+            ev = 0;
+            ef = 0;
+        }
+        if (first_row >= 0) {
+            AT tot = first_val + ev;
+            if (!ef) {  // the tile's first completed row is row r: add what earlier tiles carried
+                AT hi = carry_hi, lo = carry_lo;
+                comp_add(hi, lo, tot);
+                tot = hi + lo;
+            }
+            y[r + first_row] = (OT)tot;
+        }
+        const AT tv = __shfl_sync(FULL, v, 31);
+        if (__shfl_sync(FULL, f, 31)) {
+            carry_hi = tv;
+            carry_lo = 0;
+        } else {
+            comp_add(carry_hi, carry_lo, tv);
+        }
+        r = rn;
+        p = pn;
+        buf ^= 1;
+        __syncwarp();  // every lane is done with this tile's buffers before they are refilled
+    }
+    if (carry_row && lane == 0) {
+        // the piece ends inside row r1: hand its partial to the fix-up when it is non-empty
+        int32_t start = b.r1 < n ? __ldg(pos + b.r1) : b.p1;
+        if (start < b.p0) start = b.p0;
+        const bool has = b.p1 > start;
+        carry_row[c] = has ? b.r1 : -1;
+        carry_val[c] = has ? (double)carry_hi + (double)carry_lo : 0.0;
+    }
+}
+
 // Adds the binary64 carries of consecutive pieces that ended inside the same row to the
 // value the completing piece wrote (one thread per run of pieces).
 template <typename OT>
@@ -243,9 +554,53 @@ __global__ void carry_fixup_scalar_kernel(int64_t npieces, const int32_t *__rest
 }
 
 // Shared host path of SpMV (n rows of `pos`) and SpTTV (n = fibers, pos = pos2; the
-// row split then partitions the nouter slices of `outer` = pos1).
+// row split then partitions the nouter slices of `outer` = pos1). One warp per piece:
+// the nnz split cuts the items into pieces of kSpmvTile, the row split into P row pieces.
+template <typename VT, bool BULK>
+static spd_status launch_spmv_warp(int64_t n, int64_t nnz, const int32_t *pos, const int32_t *crd, const void *vals,
+                                   const void *x, void *y, int split, const Tuning &tn, int64_t nouter,
+                                   const int32_t *outer, void *ws, cudaStream_t st) {
+    using OT = typename Traits<VT>::out;
+    using Lay = WarpSpmvLayout<VT, kSpmvWarpIPT>;
+    constexpr int WPB = kSpmvThreads / 32;
+    const size_t smem = (size_t)WPB * Lay::bytes;
+    auto kern = spmv_warp_kernel<VT, kSpmvWarpIPT, BULK>;
+    static bool attr_set = false;  // the shared memory of binary64 tiles exceeds the 48 KiB default
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return fail(SPD_ERR_CUDA, "spmv_warp_kernel attribute: %s", cudaGetErrorString(e));
+        attr_set = true;
+    }
+    const VT *v = static_cast<const VT *>(vals);
+    const VT *xx = static_cast<const VT *>(x);
+    OT *yy = static_cast<OT *>(y);
+    if (split == SPD_SPLIT_ROW) {
+        int64_t P = tn.row_pieces;
+        if (P <= 0) P = ceil_div(n + nnz, kSpmvTile);
+        if (P < 1) P = 1;
+        kern<<<(unsigned)ceil_div(P, WPB), kSpmvThreads, smem, st>>>(n, nnz, pos, crd, v, xx, yy, nullptr, nullptr, 0,
+                                                                    P, nouter, outer, nullptr, nullptr);
+        return check_launch("spmv_warp_kernel(row)");
+    }
+    WsLayout L = layout_spmv(n, nnz, split);
+    char *w = static_cast<char *>(ws);
+    int32_t *prow = reinterpret_cast<int32_t *>(w + L.part_row);
+    int32_t *ppos = reinterpret_cast<int32_t *>(w + L.part_pos);
+    int32_t *crow = reinterpret_cast<int32_t *>(w + L.carry_row);
+    double *cval = reinterpret_cast<double *>(w + L.carry_val);
+    spd_status s = launch_merge_partition(n, nnz, pos, kSpmvTile, L.npieces, prow, ppos, st);
+    if (s) return s;
+    kern<<<(unsigned)ceil_div(L.npieces, WPB), kSpmvThreads, smem, st>>>(n, nnz, pos, crd, v, xx, yy, prow, ppos,
+                                                                        L.npieces, 0, 0, nullptr, crow, cval);
+    s = check_launch("spmv_warp_kernel(nnz)");
+    if (s) return s;
+    carry_fixup_scalar_kernel<OT><<<(unsigned)ceil_div(L.npieces, 256), 256, 0, st>>>(L.npieces, crow, cval, yy);
+    return check_launch("carry_fixup_scalar_kernel");
+}
+
+// The block-tile form: one thread block per piece (spmv_tile_kernel).
 template <typename VT>
-static spd_status launch_spmv(int64_t n, int64_t nnz, const int32_t *pos, const int32_t *crd, const void *vals,
+static spd_status launch_spmv_tile(int64_t n, int64_t nnz, const int32_t *pos, const int32_t *crd, const void *vals,
                               const void *x, void *y, int split, const Tuning &tn, int64_t nouter,
                               const int32_t *outer, void *ws, cudaStream_t st) {
     using OT = typename Traits<VT>::out;
@@ -274,6 +629,16 @@ static spd_status launch_spmv(int64_t n, int64_t nnz, const int32_t *pos, const 
     if (s) return s;
     carry_fixup_scalar_kernel<OT><<<(unsigned)ceil_div(L.npieces, 256), 256, 0, st>>>(L.npieces, crow, cval, yy);
     return check_launch("carry_fixup_scalar_kernel");
+}
+
+template <typename VT>
+static spd_status launch_spmv(int64_t n, int64_t nnz, const int32_t *pos, const int32_t *crd, const void *vals,
+                              const void *x, void *y, int split, const Tuning &tn, int64_t nouter,
+                              const int32_t *outer, void *ws, cudaStream_t st) {
+    if (tn.spmv_form != 2) return launch_spmv_tile<VT>(n, nnz, pos, crd, vals, x, y, split, tn, nouter, outer, ws, st);
+    if (aligned(crd, 16) && aligned(vals, 16))
+        return launch_spmv_warp<VT, true>(n, nnz, pos, crd, vals, x, y, split, tn, nouter, outer, ws, st);
+    return launch_spmv_warp<VT, false>(n, nnz, pos, crd, vals, x, y, split, tn, nouter, outer, ws, st);
 }
 
 static spd_status dispatch_spmv(int vtype, int64_t n, int64_t nnz, const int32_t *pos, const int32_t *crd,
@@ -325,6 +690,17 @@ spd_status spd_spmv(const spd_csr *A, const void *x, int x_type, void *y, int y_
     return checked_finish(
         dispatch_spmv(A->vtype, A->nrows, A->nnz, A->pos, A->crd, A->vals, x, y, split, tn, 0, nullptr, ws, st),
         "spd_spmv", st);
+}
+
+spd_status spd_fault_status(uint32_t *flags, void *stream) {
+    if (!flags) return fail(SPD_ERR_NULL, "flags is NULL");
+    cudaError_t e = cudaStreamSynchronize(as_stream(stream));
+    if (e != cudaSuccess) return fail(SPD_ERR_CUDA, "spd_fault_status: %s", cudaGetErrorString(e));
+    unsigned int f = 0;
+    spd_status s = take_device_faults(&f);
+    *flags = f;
+    if (s) return s;
+    return f ? fail(SPD_ERR_TIMEOUT, "a kernel's bounded wait for its bulk copies gave up (flags 0x%x)", f) : SPD_OK;
 }
 
 spd_status spd_spttv(const spd_csf3 *B, const void *c, int c_type, void *out_vals, int out_type, int split,

@@ -36,7 +36,7 @@ def test_library_exports_every_declared_function():
 
 def test_status_strings_and_version():
     lib = _abi.load()
-    assert lib.spd_abi_version() == 1
+    assert lib.spd_abi_version() == 2
     for s in range(11):
         assert lib.spd_status_str(s)
     assert lib.spd_status_str(99) == b"unknown status"

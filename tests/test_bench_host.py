@@ -1,6 +1,6 @@
 """Host-side pieces of bench.py that need no GPU: the algorithmic byte counts behind
-the roofline, the lookup of the recorded ncu traffic (valid only for the captured R-MAT
-scale, kernel sources and tuning), and the sizing of the CPU oracle sample."""
+the roofline, the record and lookup of ncu counters (valid only for the captured case,
+kernel sources and tuning), and the sizing of the CPU oracle sample."""
 import numpy as np
 
 import bench
@@ -17,14 +17,26 @@ def test_algorithmic_bytes_formulas():
     assert bench.algorithmic_bytes("spmm", n, nnz, 2, 2, 4) == b16 + 2 * n * L + 4 * n * L
 
 
-def test_recorded_traffic_only_for_the_captured_case(monkeypatch):
-    tune = {"unit_items": 1024, "block_threads": 128, "inflight": 8}
-    got = bench.recorded_traffic(tune, 22)
-    assert isinstance(got, int) and got > 10 ** 9
-    assert bench.recorded_traffic(tune, 20) is None  # another scale
-    assert bench.recorded_traffic(dict(tune, unit_items=2048), 22) is None  # another tuning
-    monkeypatch.setattr(bench, "spmm_source_hash", lambda: "0000000000000000")
-    assert bench.recorded_traffic(tune, 22) is None  # the kernel sources changed
+def test_recorded_traffic_only_for_the_captured_case(monkeypatch, tmp_path):
+    """A record written from an ncu raw CSV is returned for its kernel, case and tuning
+    while the kernel's sources are unchanged, and never otherwise."""
+    csv_path = tmp_path / "raw.csv"
+    csv_path.write_text(
+        '"ID","Kernel Name","gpu__time_duration.sum","dram__bytes_read.sum","dram__bytes_write.sum",'
+        '"lts__t_sector_hit_rate.pct"\n'
+        '"","","usecond","Gbyte","Mbyte","%"\n'
+        '"0","spmm_warp_kernel","2,900.5","15.1","480.25","41.5"\n')
+    path = str(tmp_path / "traffic.json")
+    rec = bench.record_traffic(str(csv_path), "spmm", "rmat22_f32_L128", "1024,128,8", "ncu ...", path=path)
+    assert rec["dram_bytes"] == 15_100_000_000 + 480_250_000 and rec["l2_hit_pct"] == 41.5
+    got = bench.recorded_traffic("spmm", "rmat22_f32_L128", "1024,128,8", path=path)
+    assert got["dram_bytes"] == rec["dram_bytes"]
+    assert bench.recorded_traffic("spmm", "rmat20_f32_L128", "1024,128,8", path=path) is None  # another case
+    assert bench.recorded_traffic("spmm", "rmat22_f32_L128", "2048,128,8", path=path) is None  # another tuning
+    assert bench.recorded_traffic("spmv", "rmat22_f32_L128", "1024,128,8", path=path) is None  # another kernel
+    monkeypatch.setattr(bench, "source_hash", lambda kernel: "0000000000000000")
+    assert bench.recorded_traffic("spmm", "rmat22_f32_L128", "1024,128,8", path=path) is None  # sources changed
+    assert bench.tune_key({"unit_items": 1024, "block_threads": 128, "inflight": 8}) == "1024,128,8"
 
 
 def test_cpu_sample_is_bounded_and_spans_the_rows():

@@ -147,10 +147,34 @@ def test_spmv(name, dtype):
     scale = oracle.spmv(A.pos, A.crd, np.abs(vr), np.abs(xr))
     dA = dev_csr(A, dtype)
     for split in SPLITS:
-        y = spd.spmv(dA, dev(x, dtype), split=split)
+        for form in (1, 2):  # block tiles; warp tiles with bulk copies
+            y = spd.spmv(dA, dev(x, dtype), split=split, tune={"spmv_form": form})
+            torch.cuda.synchronize()
+            assert y.dtype == spd.result_dtype(dtype)
+            check(y.double().cpu().numpy(), ref, scale, dtype, "spmv %s %s %s form %d" % (name, dtype, split, form),
+                  row_lengths(A.pos))
+
+
+@pytest.mark.parametrize("name", ["rmat12", "longrow", "empty_rows", "banded"])
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_spmv_warp_form_unaligned_operands(name, dtype):
+    """crd and vals that do not start on a 16-byte boundary (views one element into
+    larger arrays): the warp-tile form falls back from bulk copies to plain loads."""
+    A = get_mats()[name]
+    rng = np.random.default_rng(18)
+    x = rng.uniform(-1, 1, A.ncols)
+    vr, xr = rounded(A.vals, dtype), rounded(x, dtype)
+    ref = oracle.spmv(A.pos, A.crd, vr, xr, accurate=True)
+    scale = oracle.spmv(A.pos, A.crd, np.abs(vr), np.abs(xr))
+    crd_big = torch.zeros(A.nnz + 1, dtype=torch.int32, device="cuda")
+    crd_big[1:] = torch.as_tensor(A.crd).cuda()
+    val_big = torch.zeros(A.nnz + 1, dtype=dtype, device="cuda")
+    val_big[1:] = dev(A.vals, dtype)
+    dA = spd.CSR(torch.as_tensor(A.pos).cuda(), crd_big[1:], val_big[1:], (A.nrows, A.ncols))
+    for split in SPLITS:
+        y = spd.spmv(dA, dev(x, dtype), split=split, tune={"spmv_form": 2})
         torch.cuda.synchronize()
-        assert y.dtype == spd.result_dtype(dtype)
-        check(y.double().cpu().numpy(), ref, scale, dtype, "spmv %s %s %s" % (name, dtype, split),
+        check(y.double().cpu().numpy(), ref, scale, dtype, "spmv unaligned %s %s %s" % (name, dtype, split),
               row_lengths(A.pos))
 
 
@@ -167,7 +191,8 @@ def test_spmv_split_invariance_integer_exact(dtype):
     dA = spd.CSR.from_host(A.pos, A.crd, vals, (A.nrows, A.ncols), dtype=dtype)
     dx = dev(x, dtype)
     for split, tune in [("row", None), ("nnz", None), ("row", {"row_pieces": 1}), ("row", {"row_pieces": 7}),
-                        ("row", {"row_pieces": 152}), ("nnz", {"unit_items": 64})]:
+                        ("row", {"row_pieces": 152}), ("nnz", {"unit_items": 64}), ("nnz", {"spmv_form": 2}),
+                        ("row", {"spmv_form": 2}), ("row", {"spmv_form": 2, "row_pieces": 7})]:
         y = spd.spmv(dA, dx, split=split, tune=tune).double().cpu().numpy()
         assert np.array_equal(y, ref), (split, tune)
 
@@ -368,10 +393,11 @@ def test_spttv(name, dtype):
     scale = oracle.spttv(T.pos1, T.crd1, T.pos2, T.crd2, np.abs(vr), np.abs(cr))
     dT = dev_csf(T, dtype)
     for split in SPLITS:
-        out = spd.spttv(dT, dev(c, dtype), split=split)
-        torch.cuda.synchronize()
-        check(out.double().cpu().numpy(), ref, scale, dtype, "spttv %s %s %s" % (name, dtype, split),
-              row_lengths(T.pos2))
+        for form in (1, 2):
+            out = spd.spttv(dT, dev(c, dtype), split=split, tune={"spmv_form": form})
+            torch.cuda.synchronize()
+            check(out.double().cpu().numpy(), ref, scale, dtype, "spttv %s %s %s form %d" % (name, dtype, split, form),
+                  row_lengths(T.pos2))
 
 
 @pytest.mark.parametrize("name", ["zipf", "dense_small", "long_fiber", "empty_slices"])
