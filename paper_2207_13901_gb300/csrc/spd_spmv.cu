@@ -83,19 +83,30 @@ __global__ void __launch_bounds__(NT, sizeof(VT) == 2 ? 8 : 6) spmv_tile_kernel(
     }
     int32_t r = b.r0, p = b.p0;
     AT carry_hi = 0, carry_lo = 0;  // partial of row r accumulated over earlier tiles
+    for (int w = tid; w < NWORDS; w += NT) s_bits[w] = 0u;  // later tiles clear it at their end
+    __syncthreads();
 
     while (true) {
         const int64_t rem_rows = (int64_t)b.r1 - r, rem_nnz = (int64_t)b.p1 - p;
         if (rem_rows + rem_nnz == 0) break;
         const int nr = (int)(rem_rows < TILE ? rem_rows : TILE);
         const int items = (int)((rem_rows + rem_nnz) < TILE ? (rem_rows + rem_nnz) : TILE);
-        for (int w = tid; w < NWORDS; w += NT) s_bits[w] = 0u;
-        __syncthreads();
-        for (int q = tid; q < nr; q += NT) {
-            const int e = ld_stream(pos + r + 1 + q) - p + q;  // item index of row q's end
-            if (e < items) atomicOr(&s_bits[e >> 5], 1u << (e & 31));
+        // row ends of the tile, NT rows at a time: a further chunk only while the last row
+        // of the previous one still ended inside the tile (a tile of power-law rows holds
+        // about a hundred row ends; a run of empty rows can hold up to TILE)
+        if (nr == 0) __syncthreads();
+        for (int q0 = 0; q0 < nr; q0 += NT) {
+            const int q = q0 + tid;
+            bool more = false;
+            if (q < nr) {
+                const int64_t e = (int64_t)ld_stream(pos + r + 1 + q) - p + q;  // item index of row q's end
+                if (e < items) {
+                    atomicOr(&s_bits[e >> 5], 1u << (e & 31));
+                    more = q == q0 + NT - 1;
+                }
+            }
+            if (!__syncthreads_or(more)) break;
         }
-        __syncthreads();
         if (wid == 0) {  // exclusive popcount prefix of the 64 words, two per lane
             const int c0 = __popc(s_bits[2 * lane]), c1 = __popc(s_bits[2 * lane + 1]);
             int inc = c0 + c1;
@@ -135,28 +146,28 @@ __global__ void __launch_bounds__(NT, sizeof(VT) == 2 ? 8 : 6) spmv_tile_kernel(
         const int sh = k0 & 31;
         const uint32_t wbits = s_bits[word];
         const uint32_t mine = k0 < TILE ? wbits >> sh : 0u;  // bit k: item k0 + k is a row end
-        int i = s_wpre[word] + __popc(sh ? (wbits & ((1u << sh) - 1u)) : 0u);
-        int j = k0 - i;
+        const int i0 = s_wpre[word] + __popc(sh ? (wbits & ((1u << sh) - 1u)) : 0u);
+        // the thread's items in order, without branches: a row end writes the row's running
+        // sum (the first one of the thread is completed by the scan below)
+        const uint32_t valid = (k1 - k0 >= IPT) ? ((1u << IPT) - 1u) : ((1u << (k1 - k0)) - 1u);
+        const uint32_t ends = mine & valid, nzs = valid & ~mine;
         AT acc = 0, first_val = 0;
-        int first_row = -1;
+        int i = i0;
+        bool first = true;
 #pragma unroll
         for (int k = 0; k < IPT; ++k) {
-            if (k0 + k < k1) {
-                if ((mine >> k) & 1u) {  // row i ends here: all its children consumed
-                    if (first_row < 0) {
-                        first_row = i;
-                        first_val = acc;
-                    } else {
-                        y[r + i] = (OT)acc;
-                    }
-                    acc = 0;
-                    ++i;
-                } else {
-                    acc += s_prod[skew(j)];
-                    ++j;
-                }
+            const bool isend = (ends >> k) & 1u;
+            const AT pv = ((nzs >> k) & 1u) ? s_prod[skew(k0 + k - i)] : (AT)0;
+            acc += pv;
+            if (isend) {
+                if (first) first_val = acc;
+                else y[r + i] = (OT)acc;
+                first = false;
+                acc = 0;
+                ++i;
             }
         }
+        const int first_row = first ? -1 : i0;
         // block-wide segmented inclusive scan of (ended-a-row, tail partial)
         int f = first_row >= 0;
         AT v = acc;
@@ -174,14 +185,27 @@ __global__ void __launch_bounds__(NT, sizeof(VT) == 2 ? 8 : 6) spmv_tile_kernel(
             s_wv[wid] = v;
         }
         __syncthreads();
+        // segmented exclusive scan of the warps' (flag, partial) with shuffles: lane w of
+        // every warp holds warp w's pair, and each warp takes the prefix of the warps before it
         AT wp_v = 0;
         int wp_f = 0;
-        for (int w = 0; w < wid; ++w) {
-            if (s_wf[w]) {
-                wp_v = s_wv[w];
-                wp_f = 1;
-            } else {
-                wp_v += s_wv[w];
+        {
+            int sf = lane < NW ? s_wf[lane] : 0;
+            AT sv = lane < NW ? s_wv[lane] : (AT)0;
+#pragma unroll
+            for (int off = 1; off < NW; off <<= 1) {
+                const int pf = __shfl_up_sync(FULL, sf, off);
+                const AT pv = __shfl_up_sync(FULL, sv, off);
+                if (lane >= off) {
+                    if (!sf) sv += pv;
+                    sf |= pf;
+                }
+            }
+            const AT iv = __shfl_sync(FULL, sv, (wid + 31) & 31);
+            const int iff = __shfl_sync(FULL, sf, (wid + 31) & 31);
+            if (wid > 0) {
+                wp_v = iv;
+                wp_f = iff;
             }
         }
         const AT incl_v = f ? v : wp_v + v;
@@ -214,6 +238,7 @@ __global__ void __launch_bounds__(NT, sizeof(VT) == 2 ? 8 : 6) spmv_tile_kernel(
         } else {
             comp_add(carry_hi, carry_lo, tv);
         }
+        for (int w = tid; w < NWORDS; w += NT) s_bits[w] = 0u;  // every read of the bitmap is done
         r += ic;
         p += jc;
         __syncthreads();
