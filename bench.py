@@ -60,9 +60,9 @@ def parse_args(argv=None):
     p.add_argument("--record-traffic", nargs=5, metavar=("CSV", "KERNEL", "CASE", "TUNE", "COMMAND"),
                    help="store the counters of an ncu raw CSV export in profiles/traffic.json and exit")
     p.add_argument("--case", default="",
-                   help="time one kernel case alone and exit (for profiling): sddmm:K:DTYPE on the 2^20-row R-MAT "
-                        "with 32 samples per row, or spmttkrp:R:DTYPE on the Zipf CSF tensor (DTYPE f32, bf16 or "
-                        "f64; nnz split, unit 1024, 128 threads)")
+                   help="time one kernel case alone and exit (for profiling): spmv:SCALE:DTYPE:FORM, "
+                        "banded:0:DTYPE:FORM, spmm:SCALE:DTYPE, sddmm:K:DTYPE, spttv:0:DTYPE:FORM or "
+                        "spmttkrp:R:DTYPE (DTYPE f32, bf16 or f64; nnz split)")
     return p.parse_args(argv)
 
 
@@ -298,15 +298,48 @@ def error_stats(got, ref, scale):
 
 def run_case(args):
     """One kernel case timed alone (3 untimed calls, then `--steps` calls between CUDA
-    events); prints one JSON line. Small enough to run under a profiler."""
+    events); prints one JSON line. Small enough to run under a profiler. Cases:
+      spmv:SCALE:DTYPE:FORM    SpMV on the R-MAT 2^SCALE (16 samples per row), nnz split
+      banded:0:DTYPE:FORM      SpMV on the banded matrix (21.2M rows, 33 per row)
+      spmm:SCALE:DTYPE         SpMM, L = 128, on the R-MAT 2^SCALE, nnz split, unit 1024,
+                               128 threads, 8 rows in flight
+      sddmm:K:DTYPE            SDDMM on the 2^20-row R-MAT with 32 samples per row
+      spttv:0:DTYPE:FORM       SpTTV on the Zipf(1.1) CSF tensor (50M nonzeros)
+      spmttkrp:R:DTYPE         SpMTTKRP on the same tensor
+    (DTYPE f32, bf16 or f64; FORM 1 or 2 as spd_tune.spmv_form; nnz split.)"""
     import torch
     import spd_synth
     import paper_2207_13901_gb300 as spd
-    kind, width, dname = args.case.split(":")
-    width = int(width)
+    parts = args.case.split(":")
+    kind, width, dname = parts[0], int(parts[1]), parts[2]
+    form = int(parts[3]) if len(parts) > 3 else 1
     dt = {"f32": torch.float32, "bf16": torch.bfloat16, "f64": torch.float64}[dname]
     tune = {"unit_items": 1024, "block_threads": 128}
-    if kind == "sddmm":
+    if kind in ("spmv", "banded", "spmm"):
+        if kind == "banded":
+            A = spd_synth.banded_csr(21_212_122, 16, seed=4)
+            what = "SpMV on the banded matrix, %d nonzeros" % A.nnz
+        else:
+            A = spd_synth.rmat_csr(width, 16, 0.57, 0.19, 0.19, seed=0)
+            what = "%s on R-MAT 2^%d, %d nonzeros" % ("SpMV" if kind == "spmv" else "SpMM L=128", width, A.nnz)
+        n = A.nrows
+        dA = spd.CSR.from_host(A.pos, A.crd, A.vals, (n, A.ncols), dtype=dt)
+        rdt = spd.result_dtype(dt)
+        if kind == "spmm":
+            tune = dict(tune, inflight=8)
+            X = torch.from_numpy(spd_synth.uniform((A.ncols, L_COLS), seed=3, dtype=np.float32)).cuda().to(dt)
+            Y = torch.empty((n, L_COLS), dtype=rdt, device="cuda")
+            ws = torch.empty(max(spd.csr_workspace_size(1, dA, "nnz", L_COLS, tune), 1), dtype=torch.uint8,
+                             device="cuda")
+            fn = lambda: spd.spmm(dA, X, Y, split="nnz", tune=tune, ws=ws)
+        else:
+            tune = {"spmv_form": form}
+            x = torch.from_numpy(spd_synth.uniform(A.ncols, seed=2, dtype=np.float32)).cuda().to(dt)
+            y = torch.empty(n, dtype=rdt, device="cuda")
+            ws = torch.empty(max(spd.csr_workspace_size(0, dA, "nnz"), 1), dtype=torch.uint8, device="cuda")
+            fn = lambda: spd.spmv(dA, x, y, split="nnz", tune=tune, ws=ws)
+        units = A.nnz
+    elif kind == "sddmm":
         B = spd_synth.rmat_csr(20, 32, seed=0)
         n = B.nrows
         C = torch.from_numpy(spd_synth.normal((n, width), seed=10 + width, dtype=np.float32)).cuda().to(dt)
@@ -315,14 +348,22 @@ def run_case(args):
         out = torch.empty(B.nnz, dtype=spd.result_dtype(dt), device="cuda")
         fn = lambda: spd.sddmm(dB, C, D, out, split="nnz", tune=tune)
         units, what = B.nnz, "SDDMM K=%d on R-MAT 2^20 (32 samples per row), %d nonzeros" % (width, B.nnz)
-    elif kind == "spmttkrp":
+    elif kind in ("spmttkrp", "spttv"):
         T = spd_synth.zipf_csf3((1 << 17,) * 3, 50_000_000, 1.1, seed=0)
         dT = spd.CSF3.from_host(T.pos1, T.crd1, T.pos2, T.crd2, T.vals, T.dims, dtype=dt)
-        Cf = torch.from_numpy(spd_synth.normal((T.dims[1], width), seed=40 + width, dtype=np.float32)).cuda().to(dt)
-        Df = torch.from_numpy(spd_synth.normal((T.dims[2], width), seed=50 + width, dtype=np.float32)).cuda().to(dt)
-        Af = torch.empty((T.dims[0], width), dtype=spd.result_dtype(dt), device="cuda")
-        fn = lambda: spd.spmttkrp(dT, Cf, Df, Af, split="nnz", tune=tune)
-        units, what = T.nnz, "SpMTTKRP R=%d on the Zipf(1.1) CSF 2^17 x 2^17 x 2^17, %d nonzeros" % (width, T.nnz)
+        if kind == "spttv":
+            tune = {"spmv_form": form}
+            c = torch.from_numpy(spd_synth.normal(T.dims[2], seed=31, dtype=np.float32)).cuda().to(dt)
+            o = torch.empty(T.nfib, dtype=spd.result_dtype(dt), device="cuda")
+            fn = lambda: spd.spttv(dT, c, o, split="nnz", tune=tune)
+            what = "SpTTV on the Zipf(1.1) CSF 2^17 x 2^17 x 2^17, %d nonzeros" % T.nnz
+        else:
+            Cf = torch.from_numpy(spd_synth.normal((T.dims[1], width), seed=40 + width, dtype=np.float32)).cuda().to(dt)
+            Df = torch.from_numpy(spd_synth.normal((T.dims[2], width), seed=50 + width, dtype=np.float32)).cuda().to(dt)
+            Af = torch.empty((T.dims[0], width), dtype=spd.result_dtype(dt), device="cuda")
+            fn = lambda: spd.spmttkrp(dT, Cf, Df, Af, split="nnz", tune=tune)
+            what = "SpMTTKRP R=%d on the Zipf(1.1) CSF 2^17 x 2^17 x 2^17, %d nonzeros" % (width, T.nnz)
+        units = T.nnz
     else:
         raise SystemExit("unknown case %r" % args.case)
     ms = _time_ms(fn, reps=max(1, args.steps), warm=3)
