@@ -132,19 +132,23 @@ typedef struct {
  *                 side by side; 2 = one nonzero per warp step over 32 narrower lanes;
  *                 0 = the library's choice (groups when X is at most 64 MiB, so that its
  *                 rows stay in L2 and the gathers are bound by instruction issue).
- *   spmv_form     kernel form of SpMV and SpTTV: 1 = a thread block per piece with
- *                 tiles of 2048 items (little shared memory, so L1 keeps caching the
- *                 gathered x: the better form for power-law columns); 2 = a warp per
- *                 piece with tiles of 256 items whose crd/vals windows arrive by bulk
- *                 copies (TMA) one tile ahead (the better form when x is read locally,
- *                 e.g. banded matrices); 0 = the library's choice (currently 1). */
+ *   form          kernel form, 0 = the library's choice.
+ *                 SpMV and SpTTV: 1 = a thread block per piece with tiles of 2048 items
+ *                 (little shared memory, so L1 keeps caching the gathered x: the better
+ *                 form for power-law columns; the default); 2 = a warp per piece with
+ *                 tiles of 256 items whose crd/vals windows arrive by bulk copies (TMA)
+ *                 one tile ahead (the better form when x is read locally, e.g. banded
+ *                 matrices).
+ *                 SDDMM: 1 = CUDA cores (the default); 2 = tensor cores (mma.sync,
+ *                 bfloat16 values and dense operands, K a multiple of 32, 16-byte
+ *                 aligned rows; other calls take the CUDA cores). */
 typedef struct {
     int32_t unit_items;
     int32_t row_pieces;
     int32_t block_threads;
     int32_t inflight;
     int32_t lane_groups;
-    int32_t spmv_form;
+    int32_t form;
 } spd_tune;
 
 /* -------------------------------------------------------------------- misc */

@@ -47,7 +47,7 @@ class spd_tune(ctypes.Structure):
     _fields_ = [
         ("unit_items", ctypes.c_int32), ("row_pieces", ctypes.c_int32),
         ("block_threads", ctypes.c_int32), ("inflight", ctypes.c_int32), ("lane_groups", ctypes.c_int32),
-        ("spmv_form", ctypes.c_int32),
+        ("form", ctypes.c_int32),
     ]
 
 

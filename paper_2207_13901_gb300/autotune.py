@@ -48,7 +48,7 @@ def warp_candidates(include_row: bool = True, inflight: bool = True) -> List[dic
 
 def spmv_candidates() -> List[dict]:
     """Both splits with both kernel forms of SpMV (block tiles, warp tiles with bulk copies)."""
-    return [{"split": split, "tune": {"spmv_form": form}} for split in ("nnz", "row") for form in (1, 2)]
+    return [{"split": split, "tune": {"form": form}} for split in ("nnz", "row") for form in (1, 2)]
 
 
 class Autotuner:
@@ -136,5 +136,8 @@ class Autotuner:
     def sddmm(self, B: "ops.CSR", C: torch.Tensor, Dnk: torch.Tensor, force: bool = False) -> dict:
         out = torch.empty(B.nnz, dtype=ops.result_dtype(C.dtype), device=C.device)
         key = self.shape_key("sddmm", B, C.shape[1], C.dtype)
-        return self.choose(key, warp_candidates(True, inflight=False),
+        cands = warp_candidates(True, inflight=False)
+        if C.dtype == torch.bfloat16:  # CUDA cores or tensor cores
+            cands = [{"split": c["split"], "tune": dict(c["tune"] or {}, form=f)} for c in cands for f in (1, 2)]
+        return self.choose(key, cands,
                            lambda c: (lambda: ops.sddmm(B, C, Dnk, out, split=c["split"], tune=c["tune"])), force)

@@ -70,7 +70,7 @@ spd_status read_tune(const spd_tune *t, Tuning *out) {
     out->block_threads = kWarpBlockDefault;
     out->inflight = 8;
     out->lane_groups = 0;
-    out->spmv_form = 0;
+    out->form = 0;
     if (!t) return SPD_OK;
     if (t->unit_items) {
         if (t->unit_items < 32 || t->unit_items > 65536 || t->unit_items % 32)
@@ -93,8 +93,8 @@ spd_status read_tune(const spd_tune *t, Tuning *out) {
     }
     if (t->lane_groups < 0 || t->lane_groups > 2) return fail(SPD_ERR_ARG, "lane_groups %d not in 0..2", t->lane_groups);
     out->lane_groups = t->lane_groups;
-    if (t->spmv_form < 0 || t->spmv_form > 2) return fail(SPD_ERR_ARG, "spmv_form %d not in 0..2", t->spmv_form);
-    out->spmv_form = t->spmv_form;
+    if (t->form < 0 || t->form > 2) return fail(SPD_ERR_ARG, "form %d not in 0..2", t->form);
+    out->form = t->form;
     return SPD_OK;
 }
 

@@ -412,7 +412,8 @@ struct Tuning {
     int block_threads;    // threads per block (warp kernels)
     int inflight;         // dense rows in flight per group (SpMM)
     int lane_groups;      // SpMM lane shape: 0 = by the size of X, 1 = groups, 2 = 32 lanes
-    int spmv_form;        // SpMV / SpTTV kernel form: 0 = library's choice, 1 = block tiles, 2 = warp tiles
+    int form;             // kernel form (0 = library's choice): SpMV/SpTTV 1 = block tiles, 2 = warp tiles;
+                          // SDDMM 1 = CUDA cores, 2 = tensor cores
 };
 spd_status read_tune(const spd_tune *t, Tuning *out);
 int resolve_split(int split);

@@ -19,9 +19,11 @@
 // a 32-bit row index times a 32-bit byte pitch (one wide multiply-add). KT = 0 is the
 // general form for any K or pitch: both rows loaded per position, k tiles in a loop.
 //
-// The contraction over k is one dot product per stored position (a matrix-vector
-// shape, no reuse of D rows inside a warp), so it stays on the CUDA cores: at about
-// 0.5 flop per gathered byte it is bound by the gathers, not by arithmetic.
+// The contraction over k is one dot product per stored position, on the CUDA cores by
+// default. With bfloat16 operands (K a multiple of 32) form 2 runs it on the tensor cores,
+// 16 positions at a time (sddmm_mma_kernel below): parity-green, but measured slower on
+// the R-MAT workload (the kernel is bound by the gathers and their latency, not by the
+// multiply-adds), so the autotuner times both.
 #include "spd_internal.cuh"
 
 namespace spd {
@@ -165,6 +167,159 @@ __global__ void __launch_bounds__(256) sddmm_warp_kernel(
     }
 }
 
+// ------------------------------------------------------------------ tensor-core form
+//
+// bfloat16 operands with binary32 accumulation, K a multiple of 32: the contraction over
+// k of 16 consecutive positions runs on the tensor cores (mma.sync m16n8k16, bf16 inputs,
+// fp32 accumulators). A is the 16 positions' rows of Dnk (16 x 16 per k step), B holds
+// the rows of C of the distinct rows of those positions (up to 8 columns; a second pass
+// takes the 9th to 16th), and the result column of each position's own row is its dot
+// product. The order of k inside a dot product is free, so the fragment slots of a lane
+// (k slots 2t, 2t+1, 2t+8, 2t+9 of a 16-wide step, t = lane % 4) are mapped to 8
+// consecutive k of each row: every operand load is one 16-byte vector, and A and B use the
+// same map, so the sum is the dot product. Each product of two bfloat16 values is exact
+// in binary32.
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                               uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__global__ void __launch_bounds__(256) sddmm_mma_kernel(
+    int64_t n, const int32_t *__restrict__ pos, const int32_t *__restrict__ crd,
+    const __nv_bfloat16 *__restrict__ vals, const __nv_bfloat16 *__restrict__ C, uint32_t ldc_b,
+    const __nv_bfloat16 *__restrict__ Dnk, uint32_t ldd_b, int64_t K, float *__restrict__ out,
+    const int32_t *__restrict__ prow, const int32_t *__restrict__ ppos, int64_t npieces, int64_t P) {
+    const int lane = threadIdx.x & 31;
+    const int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (c >= (prow ? npieces : P)) return;  // whole warp
+    const PieceBounds b = prow ? nnz_piece(c, prow, ppos) : row_piece(c, P, n, pos);
+    const int g = lane >> 2, t = lane & 3;  // fragment row group and k slot group of this lane
+    const int ksteps = (int)(K / 32);       // 32 k per step: two m16n8k16 steps
+    const char *Db = reinterpret_cast<const char *>(Dnk) + (size_t)t * 16;
+    const char *Cb = reinterpret_cast<const char *>(C) + (size_t)t * 16;
+    auto ld16 = [](const char *p) { return __ldg(reinterpret_cast<const uint4 *>(p)); };
+
+    PosRows pr;
+    pr.load(b.r0, n, pos, lane);
+    for (int32_t pb = b.p0; pb < b.p1; pb += 32) {
+        const int cnt = (b.p1 - pb) < 32 ? (b.p1 - pb) : 32;
+        const bool valid = lane < cnt;
+        const int32_t my_crd = valid ? ld_stream(crd + pb + lane) : 0;
+        const float my_val = (valid && vals) ? __bfloat162float(__ldcs(vals + pb + lane)) : 1.f;
+        const int32_t my_row = pr.find(pb + lane, valid, n, pos, lane);
+        const int32_t next_rw = __shfl_sync(FULLM, my_row, cnt - 1);
+        if (next_rw != pr.rw) pr.load(next_rw, n, pos, lane);
+        // both halves of the window (positions 0..15 and 16..31) at once, so the gathers
+        // of 32 positions are in flight together
+        const int m = lane & 15, hb = lane >> 4;  // lane m of half hb describes position 16*hb + m
+        const int32_t rm = __shfl_sync(FULLM, my_row, 16 * hb + m);
+        const int32_t rp = __shfl_sync(FULLM, my_row, 16 * hb + (m > 0 ? m - 1 : 0));
+        const bool vm = 16 * hb + m < cnt;
+        const uint32_t st_all = __ballot_sync(FULLM, vm && (m == 0 || rm != rp));
+        uint32_t starts[2];
+        int nslots[2];
+        int32_t jg[2], jh[2], crow[2][2];
+        bool vg[2], vh[2], cv[2][2];
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+            starts[hh] = (st_all >> (16 * hh)) & 0xffffu;  // bit q: position 16*hh + q starts a row
+            nslots[hh] = __popc(starts[hh]);
+            // rows of Dnk for positions g and g + 8 of the half
+            jg[hh] = __shfl_sync(FULLM, my_crd, 16 * hh + g);
+            jh[hh] = __shfl_sync(FULLM, my_crd, 16 * hh + g + 8);
+            vg[hh] = 16 * hh + g < cnt;
+            vh[hh] = 16 * hh + g + 8 < cnt;
+            // row of C for column g of pass 0 and pass 1
+#pragma unroll
+            for (int ps = 0; ps < 2; ++ps) {
+                const unsigned at = __fns(starts[hh], 0, 8 * ps + g + 1);
+                cv[hh][ps] = at != 0xffffffffu;
+                crow[hh][ps] = __shfl_sync(FULLM, my_row, 16 * hh + (cv[hh][ps] ? (int)at : 0));
+            }
+        }
+        const bool two = nslots[0] > 8 || nslots[1] > 8;  // a second pass (warp-uniform)
+        float acc[2][2][4];
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh)
+#pragma unroll
+            for (int ps = 0; ps < 2; ++ps)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc[hh][ps][e] = 0.f;
+        const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll 1
+        for (int s = 0; s < ksteps; ++s) {
+            uint4 a[2], h[2], b0[2];
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                a[hh] = vg[hh] ? ld16(Db + (uint64_t)(uint32_t)jg[hh] * ldd_b + s * 64) : z;
+                h[hh] = vh[hh] ? ld16(Db + (uint64_t)(uint32_t)jh[hh] * ldd_b + s * 64) : z;
+                b0[hh] = cv[hh][0] ? ld16(Cb + (uint64_t)(uint32_t)crow[hh][0] * ldc_b + s * 64) : z;
+            }
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                mma_bf16_16816(acc[hh][0], a[hh].x, h[hh].x, a[hh].y, h[hh].y, b0[hh].x, b0[hh].y);
+                mma_bf16_16816(acc[hh][0], a[hh].z, h[hh].z, a[hh].w, h[hh].w, b0[hh].z, b0[hh].w);
+            }
+            if (two) {
+#pragma unroll
+                for (int hh = 0; hh < 2; ++hh) {
+                    const uint4 b1 = cv[hh][1] ? ld16(Cb + (uint64_t)(uint32_t)crow[hh][1] * ldc_b + s * 64) : z;
+                    mma_bf16_16816(acc[hh][1], a[hh].x, h[hh].x, a[hh].y, h[hh].y, b1.x, b1.y);
+                    mma_bf16_16816(acc[hh][1], a[hh].z, h[hh].z, a[hh].w, h[hh].w, b1.z, b1.w);
+                }
+            }
+        }
+        // position g's dot sits in column slot(g) of fragment row g: lane 4g + slot/2,
+        // element slot % 2 (fragment rows g + 8: elements 2 + slot % 2)
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+            const int sg = __popc(starts[hh] & ((2u << g) - 1u)) - 1;
+            const int sh = __popc(starts[hh] & ((2u << (g + 8)) - 1u)) - 1;
+            const float bg = __shfl_sync(FULLM, my_val, 16 * hh + g), bh = __shfl_sync(FULLM, my_val, 16 * hh + g + 8);
+#pragma unroll
+            for (int ps = 0; ps < 2; ++ps) {
+                const int lg = sg - 8 * ps, lh = sh - 8 * ps;
+                const float dg = (lg & 1) ? acc[hh][ps][1] : acc[hh][ps][0];  // selects: no indexed registers
+                const float dh = (lh & 1) ? acc[hh][ps][3] : acc[hh][ps][2];
+                if (vg[hh] && lg >= 0 && lg < 8 && (lg >> 1) == t) __stcs(out + pb + 16 * hh + g, bg * dg);
+                if (vh[hh] && lh >= 0 && lh < 8 && (lh >> 1) == t) __stcs(out + pb + 16 * hh + g + 8, bh * dh);
+            }
+        }
+    }
+}
+
+static spd_status launch_sddmm_mma(const spd_csr *B, const void *C, int64_t K, int64_t ldc, const void *Dnk,
+                                   int64_t ldd, void *outv, int split, const Tuning &tn, void *ws, cudaStream_t st) {
+    using BT = __nv_bfloat16;
+    const uint32_t ldc_b = (uint32_t)(ldc * 2), ldd_b = (uint32_t)(ldd * 2);
+    const int threads = tn.block_threads > 256 ? 256 : tn.block_threads;
+    const int wpb = threads / 32;
+    const BT *v = static_cast<const BT *>(B->vals);
+    const BT *cc = static_cast<const BT *>(C);
+    const BT *dd = static_cast<const BT *>(Dnk);
+    float *o = static_cast<float *>(outv);
+    if (split == SPD_SPLIT_ROW) {
+        int64_t P = tn.row_pieces > 0 ? tn.row_pieces : ceil_div(B->nrows + B->nnz, tn.unit_items);
+        if (P < 1) P = 1;
+        sddmm_mma_kernel<<<(unsigned)ceil_div(P, wpb), threads, 0, st>>>(B->nrows, B->pos, B->crd, v, cc, ldc_b, dd,
+                                                                        ldd_b, K, o, nullptr, nullptr, 0, P);
+        return check_launch("sddmm_mma_kernel(row)");
+    }
+    WsLayout Lw = layout_warp(B->nrows, B->nnz, split, tn.unit_items, 0, false);
+    char *w = static_cast<char *>(ws);
+    int32_t *prow = reinterpret_cast<int32_t *>(w + Lw.part_row);
+    int32_t *ppos = reinterpret_cast<int32_t *>(w + Lw.part_pos);
+    spd_status s = launch_merge_partition(B->nrows, B->nnz, B->pos, tn.unit_items, Lw.npieces, prow, ppos, st);
+    if (s) return s;
+    sddmm_mma_kernel<<<(unsigned)ceil_div(Lw.npieces, wpb), threads, 0, st>>>(
+        B->nrows, B->pos, B->crd, v, cc, ldc_b, dd, ldd_b, K, o, prow, ppos, Lw.npieces, 0);
+    return check_launch("sddmm_mma_kernel(nnz)");
+}
+
 template <typename VT, int EPL, int G, int KT>
 static spd_status launch_sddmm_g(const spd_csr *B, const void *C, int64_t K, int64_t ldc, const void *Dnk,
                                  int64_t ldd, void *outv, int split, const Tuning &tn, void *ws, cudaStream_t st) {
@@ -227,6 +382,12 @@ template <typename VT>
 static spd_status launch_sddmm(const spd_csr *B, const void *C, int64_t K, int64_t ldc, const void *Dnk, int64_t ldd,
                                void *outv, int split, const Tuning &tn, void *ws, cudaStream_t st) {
     constexpr int V = 16 / sizeof(VT);  // elements of one 16-byte vector
+    if constexpr (sizeof(VT) == 2) {
+        // tensor cores: K a multiple of 32, rows of C and Dnk in 16-byte vectors with pitches below 4 GiB
+        const bool mma_ok = K > 0 && K % 32 == 0 && ldc % 8 == 0 && ldd % 8 == 0 && aligned(C, 16) &&
+                            aligned(Dnk, 16) && ldc * 2 <= (int64_t)UINT32_MAX && ldd * 2 <= (int64_t)UINT32_MAX;
+        if (mma_ok && tn.form == 2) return launch_sddmm_mma(B, C, K, ldc, Dnk, ldd, outv, split, tn, ws, st);
+    }
     const bool vec = K % V == 0 && ldc % V == 0 && ldd % V == 0 && aligned(C, 16) && aligned(Dnk, 16);
     if (vec) return launch_sddmm_epl<VT, V>(B, C, K, ldc, Dnk, ldd, outv, split, tn, ws, st);
     return launch_sddmm_epl<VT, 1>(B, C, K, ldc, Dnk, ldd, outv, split, tn, ws, st);

@@ -660,7 +660,7 @@ template <typename VT>
 static spd_status launch_spmv(int64_t n, int64_t nnz, const int32_t *pos, const int32_t *crd, const void *vals,
                               const void *x, void *y, int split, const Tuning &tn, int64_t nouter,
                               const int32_t *outer, void *ws, cudaStream_t st) {
-    if (tn.spmv_form != 2) return launch_spmv_tile<VT>(n, nnz, pos, crd, vals, x, y, split, tn, nouter, outer, ws, st);
+    if (tn.form != 2) return launch_spmv_tile<VT>(n, nnz, pos, crd, vals, x, y, split, tn, nouter, outer, ws, st);
     if (aligned(crd, 16) && aligned(vals, 16))
         return launch_spmv_warp<VT, true>(n, nnz, pos, crd, vals, x, y, split, tn, nouter, outer, ws, st);
     return launch_spmv_warp<VT, false>(n, nnz, pos, crd, vals, x, y, split, tn, nouter, outer, ws, st);

@@ -61,7 +61,7 @@ def _tune(tune) -> Optional[ctypes.POINTER(_abi.spd_tune)]:
         return None
     t = _abi.spd_tune(int(tune.get("unit_items", 0)), int(tune.get("row_pieces", 0)),
                       int(tune.get("block_threads", 0)), int(tune.get("inflight", 0)),
-                      int(tune.get("lane_groups", 0)), int(tune.get("spmv_form", 0)))
+                      int(tune.get("lane_groups", 0)), int(tune.get("form", 0)))
     return ctypes.pointer(t)
 
 

@@ -148,7 +148,7 @@ def test_spmv(name, dtype):
     dA = dev_csr(A, dtype)
     for split in SPLITS:
         for form in (1, 2):  # block tiles; warp tiles with bulk copies
-            y = spd.spmv(dA, dev(x, dtype), split=split, tune={"spmv_form": form})
+            y = spd.spmv(dA, dev(x, dtype), split=split, tune={"form": form})
             torch.cuda.synchronize()
             assert y.dtype == spd.result_dtype(dtype)
             check(y.double().cpu().numpy(), ref, scale, dtype, "spmv %s %s %s form %d" % (name, dtype, split, form),
@@ -172,7 +172,7 @@ def test_spmv_warp_form_unaligned_operands(name, dtype):
     val_big[1:] = dev(A.vals, dtype)
     dA = spd.CSR(torch.as_tensor(A.pos).cuda(), crd_big[1:], val_big[1:], (A.nrows, A.ncols))
     for split in SPLITS:
-        y = spd.spmv(dA, dev(x, dtype), split=split, tune={"spmv_form": 2})
+        y = spd.spmv(dA, dev(x, dtype), split=split, tune={"form": 2})
         torch.cuda.synchronize()
         check(y.double().cpu().numpy(), ref, scale, dtype, "spmv unaligned %s %s %s" % (name, dtype, split),
               row_lengths(A.pos))
@@ -191,8 +191,8 @@ def test_spmv_split_invariance_integer_exact(dtype):
     dA = spd.CSR.from_host(A.pos, A.crd, vals, (A.nrows, A.ncols), dtype=dtype)
     dx = dev(x, dtype)
     for split, tune in [("row", None), ("nnz", None), ("row", {"row_pieces": 1}), ("row", {"row_pieces": 7}),
-                        ("row", {"row_pieces": 152}), ("nnz", {"unit_items": 64}), ("nnz", {"spmv_form": 2}),
-                        ("row", {"spmv_form": 2}), ("row", {"spmv_form": 2, "row_pieces": 7})]:
+                        ("row", {"row_pieces": 152}), ("nnz", {"unit_items": 64}), ("nnz", {"form": 2}),
+                        ("row", {"form": 2}), ("row", {"form": 2, "row_pieces": 7})]:
         y = spd.spmv(dA, dx, split=split, tune=tune).double().cpu().numpy()
         assert np.array_equal(y, ref), (split, tune)
 
@@ -316,18 +316,43 @@ def test_sddmm(name, dtype, K):
     scale = oracle.sddmm(A.pos, A.crd, np.abs(vr), np.abs(Cr), np.abs(Dr), sel=sel)
     dA = dev_csr(A, dtype)
     dC, dD = dev(C, dtype), dev(Dnk, dtype)
+    # bfloat16: CUDA cores (form 1) and tensor cores (form 2, used when K is a multiple of 32)
+    forms = (1, 2) if dtype == torch.bfloat16 else (0,)
     for split in SPLITS:
-        out = spd.sddmm(dA, dC, dD, split=split)
-        torch.cuda.synchronize()
-        got = out.double().cpu().numpy()
-        if sel is not None:
-            got = got[sel]
-        check(got, ref, scale, dtype, "sddmm %s %s K=%d %s" % (name, dtype, K, split), K, extra=1)
+        for form in forms:
+            out = spd.sddmm(dA, dC, dD, split=split, tune={"form": form})
+            torch.cuda.synchronize()
+            got = out.double().cpu().numpy()
+            if sel is not None:
+                got = got[sel]
+            check(got, ref, scale, dtype, "sddmm %s %s K=%d %s form %d" % (name, dtype, K, split, form), K, extra=1)
     # the sampling pattern alone (every B value 1)
     ref1 = oracle.sddmm(A.pos, A.crd, None, Cr, Dr, sel=sel, accurate=True)
     scale1 = oracle.sddmm(A.pos, A.crd, None, np.abs(Cr), np.abs(Dr), sel=sel)
     out = spd.sddmm(dA.with_vals(None), dC, dD).double().cpu().numpy()
     check(out if sel is None else out[sel], ref1, scale1, dtype, "sddmm pattern %s" % name, K, extra=1)
+
+
+@pytest.mark.parametrize("K", [32, 64, 256])
+def test_sddmm_tensor_cores_short_rows(K):
+    """bfloat16 on the tensor cores where 16 consecutive positions span up to 16 distinct
+    rows (rows of 0 to 3 entries): the second pass over the 9th to 16th rows, empty rows,
+    and the sampling pattern alone."""
+    rng = np.random.default_rng(19)
+    A = spd_synth.uniform_csr(5000, 3000, (0, 3), seed=7)
+    C = rng.standard_normal((A.nrows, K))
+    Dnk = rng.standard_normal((A.ncols, K))
+    dt = torch.bfloat16
+    vr, Cr, Dr = rounded(A.vals, dt), rounded(C, dt), rounded(Dnk, dt)
+    dA = dev_csr(A, dt)
+    for vals in (vr, None):
+        ref = oracle.sddmm(A.pos, A.crd, vals, Cr, Dr, accurate=True)
+        scale = oracle.sddmm(A.pos, A.crd, None if vals is None else np.abs(vals), np.abs(Cr), np.abs(Dr))
+        B = dA if vals is not None else dA.with_vals(None)
+        for split in SPLITS:
+            out = spd.sddmm(B, dev(C, dt), dev(Dnk, dt), split=split, tune={"form": 2})
+            torch.cuda.synchronize()
+            check(out.double().cpu().numpy(), ref, scale, dt, "sddmm mma short rows K=%d %s" % (K, split), K, extra=1)
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
@@ -348,10 +373,11 @@ def test_sddmm_strided_operands(dtype, K):
     wideD[:, 16:16 + K] = dev(Dnk, dtype)
     dA = dev_csr(A, dtype)
     for split in SPLITS:
-        out = spd.sddmm(dA, wideC[:, 16:16 + K], wideD[:, 16:16 + K], split=split)
-        torch.cuda.synchronize()
-        check(out.double().cpu().numpy(), ref, scale, dtype, "sddmm strided %s K=%d %s" % (dtype, K, split), K,
-              extra=1)
+        for form in ((1, 2) if dtype == torch.bfloat16 else (0,)):
+            out = spd.sddmm(dA, wideC[:, 16:16 + K], wideD[:, 16:16 + K], split=split, tune={"form": form})
+            torch.cuda.synchronize()
+            check(out.double().cpu().numpy(), ref, scale, dtype, "sddmm strided %s K=%d %s form %d" % (dtype, K, split, form),
+                  K, extra=1)
 
 
 # ------------------------------------------------------------------------------ CSF kernels
@@ -394,7 +420,7 @@ def test_spttv(name, dtype):
     dT = dev_csf(T, dtype)
     for split in SPLITS:
         for form in (1, 2):
-            out = spd.spttv(dT, dev(c, dtype), split=split, tune={"spmv_form": form})
+            out = spd.spttv(dT, dev(c, dtype), split=split, tune={"form": form})
             torch.cuda.synchronize()
             check(out.double().cpu().numpy(), ref, scale, dtype, "spttv %s %s %s form %d" % (name, dtype, split, form),
                   row_lengths(T.pos2))

@@ -84,8 +84,8 @@ def test_spmv_long_row(dtype):
     ref = oracle.spmv(A.pos, A.crd, vr, xr, accurate=True)
     scale = oracle.spmv(A.pos, A.crd, np.abs(vr), np.abs(xr))
     dA = spd.CSR.from_host(A.pos, A.crd, A.vals, (A.nrows, A.ncols), dtype=dtype)
-    for split, tune in [("nnz", None), ("row", None), ("row", {"row_pieces": 3}), ("nnz", {"spmv_form": 2}),
-                        ("row", {"spmv_form": 2, "row_pieces": 3})]:
+    for split, tune in [("nnz", None), ("row", None), ("row", {"row_pieces": 3}), ("nnz", {"form": 2}),
+                        ("row", {"form": 2, "row_pieces": 3})]:
         y = spd.spmv(dA, dev(x, dtype), split=split, tune=tune)
         check_error(y.double().cpu().numpy(), ref, scale, dtype == torch.float64, row_lengths(A.pos),
                     "spmv long row %s %s %s" % (dtype, split, tune))
@@ -172,7 +172,7 @@ def test_spttv_long_fiber(dtype):
     assert_adversarial(np.full(5000, rounded([v], dtype)[0] * rounded([xv], dtype)[0]), unit=2048)
     dT = spd.CSF3.from_host(T.pos1, T.crd1, T.pos2, T.crd2, T.vals, T.dims, dtype=dtype)
     for split, form in (("nnz", 1), ("row", 1), ("nnz", 2), ("row", 2)):
-        out = spd.spttv(dT, dev(c, dtype), split=split, tune={"spmv_form": form})
+        out = spd.spttv(dT, dev(c, dtype), split=split, tune={"form": form})
         check_error(out.double().cpu().numpy(), ref, scale, dtype == torch.float64, row_lengths(T.pos2),
                     "spttv long fiber %s %s" % (dtype, split))
 @pytest.mark.parametrize("dtype", DTYPES)
