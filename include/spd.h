@@ -391,7 +391,7 @@ typedef struct {
     int64_t count, total_pieces, L;
     int32_t vtype, epl, group, block_threads, grid, fulltile, has_nnz;
     void *ws;
-    size_t off_desc, off_pstart, off_prow, off_ppos, off_crow, off_cval;
+    size_t off_desc, off_pstart, off_prow, off_ppos, off_crow, off_cval, off_pmat;
 } spd_batch_plan;
 
 /* Workspace bytes of a batch (host only). items: host array of count entries. */

@@ -67,6 +67,7 @@ class spd_batch_plan(ctypes.Structure):
         ("ws", ctypes.c_void_p),
         ("off_desc", ctypes.c_size_t), ("off_pstart", ctypes.c_size_t), ("off_prow", ctypes.c_size_t),
         ("off_ppos", ctypes.c_size_t), ("off_crow", ctypes.c_size_t), ("off_cval", ctypes.c_size_t),
+        ("off_pmat", ctypes.c_size_t),
     ]
 
 

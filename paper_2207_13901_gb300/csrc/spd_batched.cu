@@ -5,8 +5,9 @@
 // split: fused non-zero partition of its coordinate tree) end to end into one global
 // work list. The persistent kernel runs one block group per SM; its warps take global
 // pieces g, g + W, g + 2W, ... (pieces are equal in item count, so a static stride
-// balances them), find the matrix of each piece by binary search over the pieces'
-// prefix, and run the same per-warp SpMM body as the single-matrix kernel. A second
+// balances them), read the matrix of each piece from a table the plan writes (one load
+// instead of a search over hundreds of matrices), and run the same per-warp SpMM body as
+// the single-matrix kernel. A second
 // launch adds the binary64 carries of nnz-split matrices. Both launches are stream
 // ordered, allocate nothing and do not synchronize, so a run can be captured in a CUDA
 // graph and replayed.
@@ -32,19 +33,10 @@ struct BatchDesc {
     int64_t carry_off;  // nnz split: first of its P carries
 };
 
-__device__ __forceinline__ int64_t batch_of(const int64_t *__restrict__ pstart, int64_t count, int64_t g) {
-    int64_t lo = 0, hi = count;  // pstart[lo] <= g < pstart[hi]
-    while (hi - lo > 1) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (__ldg(pstart + mid) <= g) lo = mid;
-        else hi = mid;
-    }
-    return lo;
-}
 
 template <typename VT, int EPL, int G, bool FULLTILE>
 __global__ void __launch_bounds__(256, kSpmmMinBlocks) spmm_batched_kernel(const BatchDesc *__restrict__ descs,
-                                                           const int64_t *__restrict__ pstart, int64_t count,
+                                                           const int32_t *__restrict__ pmat,
                                                            int64_t total, int64_t L, const int32_t *__restrict__ prow,
                                                            const int32_t *__restrict__ ppos, int32_t *carry_row,
                                                            double *carry_val) {
@@ -60,8 +52,7 @@ __global__ void __launch_bounds__(256, kSpmmMinBlocks) spmm_batched_kernel(const
     AT *s_val = reinterpret_cast<AT *>(batch_smem + wpb * 64 * sizeof(int32_t)) + wid * 64;
     AT *s_cmp = reinterpret_cast<AT *>(batch_smem + wpb * 64 * sizeof(int32_t)) + wpb * 64 + wid * 32 * EPL;
     for (int64_t g = (int64_t)blockIdx.x * wpb + wid; g < total; g += nwarps) {
-        const int64_t m = batch_of(pstart, count, g);
-        const BatchDesc &d = descs[m];
+        const BatchDesc &d = descs[__ldg(pmat + g)];
         const int64_t c = g - d.piece0;
         const bool nnz_split = d.split == SPD_SPLIT_NNZ;
         const PieceBounds b = nnz_split ? nnz_piece(c, prow + d.part_off, ppos + d.part_off)
@@ -83,14 +74,14 @@ __global__ void __launch_bounds__(256, kSpmmMinBlocks) spmm_batched_kernel(const
 // Adds the carries of consecutive pieces of one nnz-split matrix that ended inside the
 // same row (one warp per global piece, one lane per column).
 template <typename OT>
-__global__ void spmm_batched_fixup_kernel(const BatchDesc *__restrict__ descs, const int64_t *__restrict__ pstart,
-                                          int64_t count, int64_t total, int64_t L,
+__global__ void spmm_batched_fixup_kernel(const BatchDesc *__restrict__ descs, const int32_t *__restrict__ pmat,
+                                          int64_t total, int64_t L,
                                           const int32_t *__restrict__ carry_row,
                                           const double *__restrict__ carry_val) {
     const int64_t g = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int64_t col = (int64_t)blockIdx.y * 32 + (threadIdx.x & 31);
     if (g >= total || col >= L) return;
-    const BatchDesc &d = descs[batch_of(pstart, count, g)];
+    const BatchDesc &d = descs[pmat[g]];
     if (d.split != SPD_SPLIT_NNZ) return;
     const int64_t c = g - d.piece0;
     const int32_t *cr = carry_row + d.carry_off;
@@ -105,7 +96,7 @@ __global__ void spmm_batched_fixup_kernel(const BatchDesc *__restrict__ descs, c
 }
 
 struct BatchLayout {
-    size_t desc = 0, pstart = 0, prow = 0, ppos = 0, crow = 0, cval = 0, total = 0;
+    size_t desc = 0, pstart = 0, pmat = 0, prow = 0, ppos = 0, crow = 0, cval = 0, total = 0;
     int64_t pieces = 0, nparts = 0, ncarry = 0;
 };
 
@@ -126,6 +117,8 @@ static BatchLayout batch_layout(int64_t count, const spd_batch_item *items, int6
     off += align_up(sizeof(BatchDesc) * (size_t)(count > 0 ? count : 1));
     B.pstart = off;
     off += align_up(sizeof(int64_t) * (size_t)(count + 1));
+    B.pmat = off;  // matrix of every global piece
+    off += align_up(sizeof(int32_t) * (size_t)(B.pieces > 0 ? B.pieces : 1));
     B.prow = off;
     off += align_up(sizeof(int32_t) * (size_t)(B.nparts > 0 ? B.nparts : 1));
     B.ppos = off;
@@ -169,7 +162,7 @@ static spd_status launch_batched(const spd_batch_plan *pl, cudaStream_t st) {
     using OT = typename Traits<VT>::out;
     char *w = static_cast<char *>(pl->ws);
     const BatchDesc *descs = reinterpret_cast<const BatchDesc *>(w + pl->off_desc);
-    const int64_t *pstart = reinterpret_cast<const int64_t *>(w + pl->off_pstart);
+    const int32_t *pmat = reinterpret_cast<const int32_t *>(w + pl->off_pmat);
     const int32_t *prow = reinterpret_cast<const int32_t *>(w + pl->off_prow);
     const int32_t *ppos = reinterpret_cast<const int32_t *>(w + pl->off_ppos);
     int32_t *crow = reinterpret_cast<int32_t *>(w + pl->off_crow);
@@ -178,11 +171,11 @@ static spd_status launch_batched(const spd_batch_plan *pl, cudaStream_t st) {
     const size_t smem = (size_t)(pl->block_threads / 32) * spmm_warp_smem<VT>(EPL, G);
     dim3 grid((unsigned)pl->grid, (unsigned)ctiles);
     spmm_batched_kernel<VT, EPL, G, FULLTILE><<<grid, pl->block_threads, smem, st>>>(
-        descs, pstart, pl->count, pl->total_pieces, pl->L, prow, ppos, crow, cval);
+        descs, pmat, pl->total_pieces, pl->L, prow, ppos, crow, cval);
     spd_status s = check_launch("spmm_batched_kernel");
     if (s || !pl->has_nnz) return s;
     dim3 fgrid((unsigned)ceil_div(pl->total_pieces, 8), (unsigned)ceil_div(pl->L, 32));
-    spmm_batched_fixup_kernel<OT><<<fgrid, 256, 0, st>>>(descs, pstart, pl->count, pl->total_pieces, pl->L, crow, cval);
+    spmm_batched_fixup_kernel<OT><<<fgrid, 256, 0, st>>>(descs, pmat, pl->total_pieces, pl->L, crow, cval);
     return check_launch("spmm_batched_fixup_kernel");
 }
 
@@ -271,6 +264,7 @@ spd_status spd_spmm_batched_plan(int64_t count, const spd_batch_item *items, int
 
     std::vector<BatchDesc> descs((size_t)count);
     std::vector<int64_t> pstart((size_t)count + 1);
+    std::vector<int32_t> pmat((size_t)B.pieces);
     int64_t piece = 0, part = 0, carry = 0;
     bool has_nnz = false;
     for (int64_t m = 0; m < count; ++m) {
@@ -299,6 +293,7 @@ spd_status spd_spmm_batched_plan(int64_t count, const spd_batch_item *items, int
             has_nnz = true;
         }
         pstart[(size_t)m] = piece;
+        for (int64_t q = 0; q < P; ++q) pmat[(size_t)(piece + q)] = (int32_t)m;
         piece += P;
     }
     pstart[(size_t)count] = piece;
@@ -307,6 +302,8 @@ spd_status spd_spmm_batched_plan(int64_t count, const spd_batch_item *items, int
     if (count > 0) e = cudaMemcpyAsync(w + B.desc, descs.data(), sizeof(BatchDesc) * descs.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(w + B.pstart, pstart.data(), sizeof(int64_t) * pstart.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && piece > 0)
+        e = cudaMemcpyAsync(w + B.pmat, pmat.data(), sizeof(int32_t) * pmat.size(), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return fail(SPD_ERR_CUDA, "plan copy: %s", cudaGetErrorString(e));
     int32_t *prow = reinterpret_cast<int32_t *>(w + B.prow);
     int32_t *ppos = reinterpret_cast<int32_t *>(w + B.ppos);
@@ -348,6 +345,7 @@ spd_status spd_spmm_batched_plan(int64_t count, const spd_batch_item *items, int
     plan->ws = ws;
     plan->off_desc = B.desc;
     plan->off_pstart = B.pstart;
+    plan->off_pmat = B.pmat;
     plan->off_prow = B.prow;
     plan->off_ppos = B.ppos;
     plan->off_crow = B.crow;
