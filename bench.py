@@ -306,7 +306,7 @@ def run_case(args):
       sddmm:K:DTYPE            SDDMM on the 2^20-row R-MAT with 32 samples per row
       spttv:0:DTYPE:FORM       SpTTV on the Zipf(1.1) CSF tensor (50M nonzeros)
       spmttkrp:R:DTYPE         SpMTTKRP on the same tensor
-    (DTYPE f32, bf16 or f64; FORM 1 or 2 as spd_tune.spmv_form; nnz split.)"""
+    (DTYPE f32, bf16 or f64; FORM 1 or 2 as spd_tune.form; nnz split.)"""
     import torch
     import spd_synth
     import paper_2207_13901_gb300 as spd
@@ -333,7 +333,7 @@ def run_case(args):
                              device="cuda")
             fn = lambda: spd.spmm(dA, X, Y, split="nnz", tune=tune, ws=ws)
         else:
-            tune = {"spmv_form": form}
+            tune = {"form": form}
             x = torch.from_numpy(spd_synth.uniform(A.ncols, seed=2, dtype=np.float32)).cuda().to(dt)
             y = torch.empty(n, dtype=rdt, device="cuda")
             ws = torch.empty(max(spd.csr_workspace_size(0, dA, "nnz"), 1), dtype=torch.uint8, device="cuda")
@@ -352,7 +352,7 @@ def run_case(args):
         T = spd_synth.zipf_csf3((1 << 17,) * 3, 50_000_000, 1.1, seed=0)
         dT = spd.CSF3.from_host(T.pos1, T.crd1, T.pos2, T.crd2, T.vals, T.dims, dtype=dt)
         if kind == "spttv":
-            tune = {"spmv_form": form}
+            tune = {"form": form}
             c = torch.from_numpy(spd_synth.normal(T.dims[2], seed=31, dtype=np.float32)).cuda().to(dt)
             o = torch.empty(T.nfib, dtype=spd.result_dtype(dt), device="cuda")
             fn = lambda: spd.spttv(dT, c, o, split="nnz", tune=tune)

@@ -35,6 +35,25 @@ struct RowWindow {
     __device__ __forceinline__ int32_t end_of(int32_t r) const { return __shfl_sync(kFullMask, true_end, r - rw); }
 };
 
+// The U values of a group from this warp's shared window (p aligned to U elements):
+// 16-byte reads.
+template <int U>
+__device__ __forceinline__ void ld_window(const float *p, float (&v)[U]) {
+#pragma unroll
+    for (int q = 0; q < U / 4; ++q) {
+        const float4 t = *reinterpret_cast<const float4 *>(p + 4 * q);
+        v[4 * q] = t.x; v[4 * q + 1] = t.y; v[4 * q + 2] = t.z; v[4 * q + 3] = t.w;
+    }
+}
+template <int U>
+__device__ __forceinline__ void ld_window(const double *p, double (&v)[U]) {
+#pragma unroll
+    for (int q = 0; q < U / 2; ++q) {
+        const double2 t = *reinterpret_cast<const double2 *>(p + 2 * q);
+        v[2 * q] = t.x; v[2 * q + 1] = t.y;
+    }
+}
+
 // One piece [b.r0, b.p0) -> [b.r1, b.p1) of matrix (n, pos, crd, vals) times X into Y.
 // s_crd / s_val: this warp's two 32-entry windows in shared memory. carry_row /
 // carry_val (nullable): where the partial of row b.r1 goes when the piece ends inside it.
@@ -130,8 +149,7 @@ __device__ __forceinline__ void spmm_piece(int64_t n, const int32_t *__restrict_
                     else zero(xv[u]);
                 }
             }
-#pragma unroll
-            for (int u = 0; u < U; ++u) vj[u] = wv[j0 + u];
+            ld_window<U>(wv + j0, vj);
             if (!kahan && gcnt == U && (int64_t)pb + j0 + U <= (int64_t)cur_end) {
                 // fast path: the whole group lies inside the current row
 #pragma unroll
@@ -304,8 +322,7 @@ __device__ __forceinline__ void spmm_piece_grouped(int64_t n, const int32_t *__r
                     else xv[u].clear();
                 }
             }
-#pragma unroll
-            for (int u = 0; u < U; ++u) vj[u] = wv[sb + u];
+            ld_window<U>(wv + sb, vj);
             if (!kahan && gcnt == STEP && (int64_t)pb + j0 + STEP <= (int64_t)cur_end) {
                 // fast path: the whole step lies inside the current row
 #pragma unroll
