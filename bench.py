@@ -61,7 +61,7 @@ def parse_args(argv=None):
                    help="store the counters of an ncu raw CSV export in profiles/traffic.json and exit")
     p.add_argument("--case", default="",
                    help="time one kernel case alone and exit (for profiling): spmv:SCALE:DTYPE:FORM, "
-                        "banded:0:DTYPE:FORM, spmm:SCALE:DTYPE, sddmm:K:DTYPE, spttv:0:DTYPE:FORM or "
+                        "banded:0:DTYPE:FORM, spmm:SCALE:DTYPE, sddmm:K:DTYPE:FORM, spttv:0:DTYPE:FORM or "
                         "spmttkrp:R:DTYPE (DTYPE f32, bf16 or f64; nnz split)")
     return p.parse_args(argv)
 
@@ -160,18 +160,19 @@ def source_hash(kernel: str) -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel: str, case: str, tune: str, path: str = TRAFFIC_JSON):
+def recorded_traffic(kernel: str, case: str, tune=None, path: str = TRAFFIC_JSON):
     """ncu counters of one launch of `kernel` on `case` (DRAM bytes read + written, L2 hit
-    rate) from the committed record, if it was taken on the current kernel sources and the
-    same tuning; otherwise None."""
+    rate) from the committed record, if it was taken on the current kernel sources (and,
+    when `tune` is given, with that tuning); otherwise None."""
     try:
         with open(path) as f:
             rec = json.load(f).get("records", {}).get(kernel + "|" + case)
     except (OSError, ValueError):
         return None
-    if not rec or rec.get("source_hash") != source_hash(kernel) or rec.get("tune") != tune:
+    if not rec or rec.get("source_hash") != source_hash(kernel) or (tune is not None and rec.get("tune") != tune):
         return None
-    return {"dram_bytes": int(rec["dram_bytes"]), "l2_hit_pct": rec.get("l2_hit_pct"), "kernel_name": rec.get("kernel_name")}
+    return {"dram_bytes": int(rec["dram_bytes"]), "l2_hit_pct": rec.get("l2_hit_pct"), "tune": rec.get("tune"),
+            "kernel_name": rec.get("kernel_name"), "duration_us_under_ncu": rec.get("duration_us_under_ncu")}
 
 
 def tune_key(tune) -> str:
@@ -303,21 +304,21 @@ def run_case(args):
       banded:0:DTYPE:FORM      SpMV on the banded matrix (21.2M rows, 33 per row)
       spmm:SCALE:DTYPE         SpMM, L = 128, on the R-MAT 2^SCALE, nnz split, unit 1024,
                                128 threads, 8 rows in flight
-      sddmm:K:DTYPE            SDDMM on the 2^20-row R-MAT with 32 samples per row
+      sddmm:K:DTYPE:FORM       SDDMM on the 2^20-row R-MAT with 32 samples per row
       spttv:0:DTYPE:FORM       SpTTV on the Zipf(1.1) CSF tensor (50M nonzeros)
       spmttkrp:R:DTYPE         SpMTTKRP on the same tensor
-    (DTYPE f32, bf16 or f64; FORM 1 or 2 as spd_tune.form; nnz split.)"""
+    (DTYPE f32, bf16 or f64; FORM 0, 1 or 2 as spd_tune.form; nnz split.)"""
     import torch
     import spd_synth
     import paper_2207_13901_gb300 as spd
     parts = args.case.split(":")
     kind, width, dname = parts[0], int(parts[1]), parts[2]
-    form = int(parts[3]) if len(parts) > 3 else 1
+    form = int(parts[3]) if len(parts) > 3 else 0
     dt = {"f32": torch.float32, "bf16": torch.bfloat16, "f64": torch.float64}[dname]
     tune = {"unit_items": 1024, "block_threads": 128}
     if kind in ("spmv", "banded", "spmm"):
         if kind == "banded":
-            A = spd_synth.banded_csr(21_212_122, 16, seed=4)
+            A = spd_synth.banded_csr(21_212_122, 16, seed=0, value_dtype=np.float32)
             what = "SpMV on the banded matrix, %d nonzeros" % A.nnz
         else:
             A = spd_synth.rmat_csr(width, 16, 0.57, 0.19, 0.19, seed=0)
@@ -346,6 +347,7 @@ def run_case(args):
         D = torch.from_numpy(spd_synth.normal((n, width), seed=20 + width, dtype=np.float32)).cuda().to(dt)
         dB = spd.CSR.from_host(B.pos, B.crd, B.vals, (n, n), dtype=dt)
         out = torch.empty(B.nnz, dtype=spd.result_dtype(dt), device="cuda")
+        tune = dict(tune, form=form)
         fn = lambda: spd.sddmm(dB, C, D, out, split="nnz", tune=tune)
         units, what = B.nnz, "SDDMM K=%d on R-MAT 2^20 (32 samples per row), %d nonzeros" % (width, B.nnz)
     elif kind in ("spmttkrp", "spttv"):
@@ -472,6 +474,8 @@ def run_gpu(args):
     spmm_gbs = spmm_bytes / (spmm_ms * 1e-3) / 1e9
     spmm_rec = (recorded_traffic("spmm", "rmat%d_f32_L%d" % (args.scale, L_COLS), tune_key(tu_m))
                 if sp_m == "nnz" else None)
+    spmv_rec = (recorded_traffic("spmv", "rmat%d_f32_form%d" % (args.scale, (tu_v or {}).get("form", 1) or 1))
+                if sp_v == "nnz" else None)
 
     # ---------------- errors of the measured step (sampled rows vs the compensated oracle)
     rng = np.random.default_rng(0)
@@ -692,6 +696,8 @@ def run_gpu(args):
                 "algorithmic_bytes": spmm_bytes,
                 "spmv_achieved": round(spmv_bytes / (spmv_ms * 1e-3) / 1e9, 1),
                 "spmv_frac": round(spmv_bytes / (spmv_ms * 1e-3) / 1e9 / hbm, 4),
+                "spmv_traffic": (spmv_rec or {}).get("dram_bytes"),
+                "spmv_l2_hit_pct": (spmv_rec or {}).get("l2_hit_pct"),
             },
             "error": step_err,
             "e2e": {"value": e2e_units / e2e_secs, "unit": "nnz/s", "h2d_bytes_per_step": h2d,
@@ -884,14 +890,16 @@ def row_banded(hbm):
         xd = torch.from_numpy(x).cuda().to(dt)
         y = torch.empty(n, dtype=spd.result_dtype(dt), device="cuda")
         s = dA.vals.element_size()
-        for split in ("nnz", "row"):
-            ms = _time_ms(lambda: spd.spmv(dA, xd, y, split=split), reps=10)
+        for split, form in (("nnz", 1), ("nnz", 2), ("row", 1)):
+            tune = {"form": form}
+            ms = _time_ms(lambda: spd.spmv(dA, xd, y, split=split, tune=tune), reps=10)
             e = _entry(ms, A.nnz, algorithmic_bytes("spmv", n, A.nnz, s, s, y.element_size()), hbm)
             vr, xr = _rounded(svals, dt), _rounded(x.astype(np.float64), dt)
             ref = oracle.spmv(spos, scrd, vr, xr, accurate=True)
             sc = oracle.spmv(spos, scrd, np.abs(vr), np.abs(xr))
             e["error"] = error_stats(y[torch.from_numpy(sel).cuda()].double().cpu().numpy(), ref, sc)
-            out["spmv_%s_%s" % (name, split)] = e
+            e["ncu"] = recorded_traffic("spmv", "banded_%s_form%d" % (name, form)) if split == "nnz" else None
+            out["spmv_%s_%s_form%d" % (name, split, form)] = e
         del dA, xd, y
         torch.cuda.empty_cache()
     x64 = x.astype(np.float64)
@@ -938,6 +946,7 @@ def row_sddmm(hbm):
             ref = oracle.sddmm(B.pos, B.crd, vr, Cr, Dr, sel=sel, accurate=True)
             sc = oracle.sddmm(B.pos, B.crd, np.abs(vr), np.abs(Cr), np.abs(Dr), sel=sel)
             e["error"] = error_stats(res.double().cpu().numpy()[sel], ref, sc)
+            e["ncu"] = recorded_traffic("sddmm", "rmat20_k%d_%s" % (K, name))
             out["K%d_%s" % (K, name)] = e
             del dB, Cd, Dd, res
         if K == 128:
@@ -1039,6 +1048,7 @@ def row_csf(hbm):
             ref = oracle.spttv(T.pos1, T.crd1, T.pos2, T.crd2, vr, cr, sel=fsel, accurate=True)
             sc = oracle.spttv(T.pos1, T.crd1, T.pos2, T.crd2, np.abs(vr), np.abs(cr), sel=fsel)
             e["error"] = error_stats(o.double().cpu().numpy()[fsel], ref, sc)
+            e["ncu"] = recorded_traffic("spttv", "zipf_%s_form1" % name) if split == "nnz" else None
             out["spttv_%s_%s" % (name, split)] = e
         for R in (32, 64):
             C = spd_synth.normal((J, R), seed=40 + R, dtype=np.float32)
@@ -1054,6 +1064,7 @@ def row_csf(hbm):
                 ref = oracle.spmttkrp(T.pos1, T.crd1, T.pos2, T.crd2, vr, Cr, Dr, sel=ssel, accurate=True)
                 sc = oracle.spmttkrp(T.pos1, T.crd1, T.pos2, T.crd2, np.abs(vr), np.abs(Cr), np.abs(Dr), sel=ssel)
                 e["error"] = error_stats(Ao.double().cpu().numpy()[ssel], ref, sc)
+                e["ncu"] = recorded_traffic("spmttkrp", "zipf_r%d_%s" % (R, name)) if split == "nnz" else None
                 out["spmttkrp_R%d_%s_%s" % (R, name, split)] = e
             del Cd, Dd, Ao
         del dT, o
