@@ -183,7 +183,7 @@ def tune_key(tune) -> str:
 
 def record_traffic(csv_path: str, kernel: str, case: str, tune: str, command: str, path: str = TRAFFIC_JSON) -> dict:
     """Stores the counters of the last launch in an ncu raw CSV export (``ncu -i REPORT
-    --page raw --csv``): dram__bytes_read.sum + dram__bytes_write.sum and
+    --page raw --csv``): dram__bytes_read.sum + dram__bytes_write.sum and, when captured,
     lts__t_sector_hit_rate.pct, with the hash of the kernel's sources and the tuning."""
     import csv
     with open(csv_path) as f:
@@ -198,8 +198,10 @@ def record_traffic(csv_path: str, kernel: str, case: str, tune: str, command: st
 
     rec = {"kernel_name": last[col["Kernel Name"]] if "Kernel Name" in col else "",
            "dram_bytes": int(val("dram__bytes_read.sum") + val("dram__bytes_write.sum")),
-           "l2_hit_pct": round(val("lts__t_sector_hit_rate.pct"), 2),
-           "duration_us_under_ncu": round(val("gpu__time_duration.sum") / (1e3 if units[col["gpu__time_duration.sum"]] == "nsecond" else 1), 2),
+           "l2_hit_pct": round(val("lts__t_sector_hit_rate.pct"), 2) if "lts__t_sector_hit_rate.pct" in col else None,
+           "duration_us_under_ncu": round(val("gpu__time_duration.sum") * {"nsecond": 1e-3, "usecond": 1.0, "msecond": 1e3,
+                                                                             "ms": 1e3, "us": 1.0, "ns": 1e-3}.get(
+               units[col["gpu__time_duration.sum"]], 1.0), 2),
            "tune": tune, "source_hash": source_hash(kernel), "command": command}
     try:
         with open(path) as f:
