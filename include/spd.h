@@ -123,7 +123,7 @@ typedef struct {
  *                 for the warp-per-unit kernels (SpMM, SpMM^T, SDDMM, SpMTTKRP);
  *                 must be a multiple of 32 in [32, 65536].
  *   row_pieces    number of pieces P of SPD_SPLIT_ROW (1 <= P <= 2^31-1).
- *   block_threads threads per block for the warp-per-unit kernels: 64..256,
+ *   block_threads threads per block for the warp-per-unit kernels: 64..512,
  *                 multiple of 32.
  *   inflight      dense rows a warp keeps in flight per group in SpMM (4 or 8;
  *                 binary64 always uses 4).

@@ -35,7 +35,7 @@ def warp_candidates(include_row: bool = True, inflight: bool = True) -> List[dic
     """Settings of the warp-per-unit kernels (SpMM, SpMM^T, SDDMM, SpMTTKRP)."""
     out = []
     for unit in (512, 1024, 2048, 4096):
-        for bt in (128, 256):
+        for bt in (128, 256, 512):
             for inf in ((4, 8) if inflight else (0,)):
                 t = {"unit_items": unit, "block_threads": bt}
                 if inf:
@@ -82,6 +82,16 @@ class Autotuner:
         return "%s|%s|n%d|nnz%d|max%d|w%d|%s" % (op, str(dtype).replace("torch.", ""), _bucket(A.shape[0]),
                                                 _bucket(A.nnz), _bucket(maxrow), width, dev)
 
+    @staticmethod
+    def csf_key(op: str, B: "ops.CSF3", width: int, dtype: torch.dtype) -> str:
+        """Shape class of a CSF operand: log2 buckets of slices, fibers, entries and the
+        largest slice (in entries), with the dense width and the device."""
+        ends = B.pos2[B.pos1.long()].long()
+        maxsl = int((ends[1:] - ends[:-1]).max().item()) if B.dims[0] > 0 else 0
+        dev = torch.cuda.get_device_name(B.pos1.device)
+        return "%s|%s|i%d|f%d|nnz%d|max%d|w%d|%s" % (op, str(dtype).replace("torch.", ""), _bucket(B.dims[0]),
+                                                     _bucket(B.nfib), _bucket(B.nnz), _bucket(maxsl), width, dev)
+
     def _time(self, fn: Callable[[], None], reps: int) -> float:
         stream = torch.cuda.current_stream()
         fn()  # warm-up (also allocates the workspace)
@@ -120,11 +130,9 @@ class Autotuner:
         key = self.shape_key("spmm", A, X.shape[1], A.dtype)
         cands = warp_candidates(True, inflight=A.dtype != torch.float64)
         if X.shape[1] * X.element_size() < 32 * 16:
-            # narrow L: both lane shapes (32 narrow lanes, or groups of 16-byte lanes)
-            for c in list(cands):
-                if c["tune"] is not None:
-                    for g in (1, 2):
-                        cands.append({"split": c["split"], "tune": dict(c["tune"], lane_groups=g)})
+            # narrow L: both lane shapes (groups of 16-byte lanes, or 32 narrower lanes)
+            cands = [{"split": c["split"], "tune": dict(c["tune"], lane_groups=g) if c["tune"] else None}
+                     for c in cands for g in ((1, 2) if c["tune"] else (0,))]
         return self.choose(key, cands, lambda c: (lambda: ops.spmm(A, X, Y, split=c["split"], tune=c["tune"])), force)
 
     def spmv(self, A: "ops.CSR", x: torch.Tensor, y: Optional[torch.Tensor] = None, force: bool = False) -> dict:
@@ -141,3 +149,21 @@ class Autotuner:
             cands = [{"split": c["split"], "tune": dict(c["tune"] or {}, form=f)} for c in cands for f in (1, 2)]
         return self.choose(key, cands,
                            lambda c: (lambda: ops.sddmm(B, C, Dnk, out, split=c["split"], tune=c["tune"])), force)
+
+    def spmm_t(self, A: "ops.CSR", dY: torch.Tensor, force: bool = False) -> dict:
+        dX = torch.empty((A.shape[1], dY.shape[1]), dtype=ops.result_dtype(A.dtype), device=dY.device)
+        key = self.shape_key("spmm_t", A, dY.shape[1], A.dtype)
+        return self.choose(key, warp_candidates(True, inflight=False),
+                           lambda c: (lambda: ops.spmm_t(A, dY, dX, split=c["split"], tune=c["tune"])), force)
+
+    def spttv(self, B: "ops.CSF3", c: torch.Tensor, force: bool = False) -> dict:
+        out = torch.empty(B.nfib, dtype=ops.result_dtype(B.dtype), device=c.device)
+        key = self.csf_key("spttv", B, 1, B.dtype)
+        return self.choose(key, spmv_candidates(),
+                           lambda k: (lambda: ops.spttv(B, c, out, split=k["split"], tune=k["tune"])), force)
+
+    def spmttkrp(self, B: "ops.CSF3", C: torch.Tensor, D: torch.Tensor, force: bool = False) -> dict:
+        A = torch.empty((B.dims[0], C.shape[1]), dtype=ops.result_dtype(B.dtype), device=C.device)
+        key = self.csf_key("spmttkrp", B, C.shape[1], B.dtype)
+        return self.choose(key, warp_candidates(True, inflight=False),
+                           lambda k: (lambda: ops.spmttkrp(B, C, D, A, split=k["split"], tune=k["tune"])), force)

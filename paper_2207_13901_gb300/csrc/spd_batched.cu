@@ -35,7 +35,7 @@ struct BatchDesc {
 
 
 template <typename VT, int EPL, int G, bool FULLTILE>
-__global__ void __launch_bounds__(256, kSpmmMinBlocks) spmm_batched_kernel(const BatchDesc *__restrict__ descs,
+__global__ void __launch_bounds__(kWarpBlockMax, kSpmmMinBlocks) spmm_batched_kernel(const BatchDesc *__restrict__ descs,
                                                            const int32_t *__restrict__ pmat,
                                                            int64_t total, int64_t L, const int32_t *__restrict__ prow,
                                                            const int32_t *__restrict__ ppos, int32_t *carry_row,

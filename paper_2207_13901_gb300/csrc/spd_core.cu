@@ -83,8 +83,9 @@ spd_status read_tune(const spd_tune *t, Tuning *out) {
     }
     if (t->block_threads) {
         // the warp kernels are compiled for blocks of at most 256 threads
-        if (t->block_threads < 64 || t->block_threads > 256 || t->block_threads % 32)
-            return fail(SPD_ERR_ARG, "block_threads %d not a multiple of 32 in [64, 256]", t->block_threads);
+        if (t->block_threads < 64 || t->block_threads > kWarpBlockMax || t->block_threads % 32)
+            return fail(SPD_ERR_ARG, "block_threads %d not a multiple of 32 in [64, %d]", t->block_threads,
+                        kWarpBlockMax);
         out->block_threads = t->block_threads;
     }
     if (t->inflight) {

@@ -405,6 +405,7 @@ constexpr int kSpmvIPT = 8;         // items per thread of one tile
 constexpr int kSpmvTile = kSpmvThreads * kSpmvIPT;
 constexpr int kWarpUnitDefault = 2048;  // items per warp unit (warp-per-unit kernels)
 constexpr int kWarpBlockDefault = 256;
+constexpr int kWarpBlockMax = 512;      // largest block of the warp-per-unit kernels
 
 struct Tuning {
     int64_t unit_items;   // warp-unit size of SPD_SPLIT_NNZ (warp kernels)

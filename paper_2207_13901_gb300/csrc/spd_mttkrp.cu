@@ -52,10 +52,19 @@ __global__ void slice_partition_kernel(int64_t I, const int32_t *__restrict__ po
     pslice[c] = (int32_t)lo;
 }
 
-// 4 resident blocks of 256 threads (64 registers): measured faster than 3 blocks with
-// the compensation kept spill-free (73 registers).
+// 32 resident warps a SM (64 registers): measured faster than 24 with the compensation
+// kept spill-free (73 registers).
+constexpr int kMttkrpResidentWarps = 32;
+
+// Shared memory of one warp: the values and Kahan compensations of a window (AT), then
+// its j, k and slice (int32).
+template <typename VT>
+inline size_t mttkrp_warp_smem(int epl) {
+    return 32 * (1 + (size_t)epl) * sizeof(typename Traits<VT>::acc) + 3 * 32 * sizeof(int32_t);
+}
+
 template <typename VT, int EPL, int G>
-__global__ void __launch_bounds__(256, 4) spmttkrp_warp_kernel(
+__global__ void __launch_bounds__(kWarpBlockMax, kMttkrpResidentWarps * 32 / kWarpBlockMax) spmttkrp_warp_kernel(
     int64_t I, int64_t F, const int32_t *__restrict__ pos1, const int32_t *__restrict__ crd1,
     const int32_t *__restrict__ pos2, const int32_t *__restrict__ crd2, const VT *__restrict__ vals,
     const VT *__restrict__ C, uint32_t ldc_b, const VT *__restrict__ D, uint32_t ldd_b, int64_t R,
@@ -66,9 +75,7 @@ __global__ void __launch_bounds__(256, 4) spmttkrp_warp_kernel(
     using OT = typename Traits<VT>::out;
     constexpr int NPG = 32 / G;         // entries per warp step
     constexpr int U = 4;  // warp steps in flight
-    __shared__ int32_t s_j_all[8][32], s_k_all[8][32], s_sl_all[8][32];
-    __shared__ AT s_v_all[8][32];
-    __shared__ AT s_cmp_all[8][EPL * 32];  // Kahan compensations of a long slice, element e at [e * 32 + lane]
+    extern __shared__ __align__(16) unsigned char mttkrp_smem[];
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
     const int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid;
@@ -96,15 +103,21 @@ __global__ void __launch_bounds__(256, 4) spmttkrp_warp_kernel(
         p1 = __ldg(pos2 + f1);
     }
     (void)f1;
-    int32_t *s_j = s_j_all[wid], *s_k = s_k_all[wid], *s_sl = s_sl_all[wid];
-    AT *s_v = s_v_all[wid];
-    AT *cmp = s_cmp_all[wid] + lane;  // compensation of element e at cmp[32 * e]
+    AT *s_v = reinterpret_cast<AT *>(mttkrp_smem) + wid * 32 * (1 + EPL);
+    AT *cmp = s_v + 32 + lane;  // Kahan compensation of element e of a long slice at cmp[32 * e]
+    int32_t *s_j = reinterpret_cast<int32_t *>(mttkrp_smem + (blockDim.x >> 5) * 32 * (1 + EPL) * sizeof(AT)) + wid * 96;
+    int32_t *s_k = s_j + 32, *s_sl = s_j + 64;
 
     AT acc[EPL];
 #pragma unroll
     for (int e = 0; e < EPL; ++e) acc[e] = 0;
     bool dirty = false;  // acc holds contributions
     int32_t cs = s0;     // slice being accumulated (the same in every lane)
+    // A window whose last entry lies in slice cs lies wholly in it and needs no slice
+    // search. Taken for bfloat16 operands only: with binary32 operands the extra live
+    // values spill at the 64-register cap and the kernel measured slower.
+    constexpr bool kSkipSearch = sizeof(VT) == 2;
+    int32_t cs_end = kSkipSearch && cs < I ? __ldg(pos1 + cs + 1) : INT_MAX;  // its end, in fibers
     // whether slice s holds more than kLongSlice entries (binary32 accumulation only);
     // the same four loads in every lane of the warp
     constexpr bool kComp = sizeof(AT) == 4;  // binary64 sums need no compensation
@@ -146,6 +159,7 @@ __global__ void __launch_bounds__(256, 4) spmttkrp_warp_kernel(
         for (int e = 0; e < EPL; ++e) acc[e] = 0;
         dirty = false;
         cs = next;
+        if (kSkipSearch) cs_end = cs < I ? __ldg(pos1 + cs + 1) : INT_MAX;
         ka = long_slice(cs);
         if (kComp && ka) clear_cmp();
     };
@@ -159,7 +173,10 @@ __global__ void __launch_bounds__(256, 4) spmttkrp_warp_kernel(
         const int32_t my_k = valid ? ld_stream(crd2 + pb + lane) : 0;
         const AT my_v = valid ? (AT)ld_stream(vals + pb + lane) : (AT)0;
         const int32_t my_f = fw.find(pb + lane, valid, F, pos2, lane);
-        const int32_t my_sl = sw.find(my_f, valid, I, pos1, lane);
+        const int32_t nf = __shfl_sync(0xffffffffu, my_f, cnt - 1);
+        // every entry of the window lies at or after slice cs, so when the last one lies
+        // before cs_end they all lie in slice cs
+        const int32_t my_sl = kSkipSearch && nf < cs_end ? cs : sw.find(my_f, valid, I, pos1, lane);
         const int32_t my_j = valid ? __ldg(crd1 + my_f) : 0;
         __syncwarp();
         s_j[lane] = my_j;
@@ -167,7 +184,6 @@ __global__ void __launch_bounds__(256, 4) spmttkrp_warp_kernel(
         s_sl[lane] = my_sl;
         s_v[lane] = my_v;
         __syncwarp();
-        const int32_t nf = __shfl_sync(0xffffffffu, my_f, cnt - 1);
         const int32_t ns = __shfl_sync(0xffffffffu, my_sl, cnt - 1);
         if (nf != fw.rw) fw.load(nf, F, pos2, lane);
         if (ns != sw.rw) sw.load(ns, I, pos1, lane);
@@ -253,8 +269,9 @@ static spd_status launch_mttkrp_g(const spd_csf3 *B, const void *C, int64_t ldc,
                                   int64_t R, void *A, int64_t lda, int split, const Tuning &tn, void *ws,
                                   cudaStream_t st) {
     using OT = typename Traits<VT>::out;
-    const int threads = tn.block_threads > 256 ? 256 : tn.block_threads;  // shared windows for <= 8 warps
+    const int threads = tn.block_threads;
     const int wpb = threads / 32;
+    const size_t smem = (size_t)wpb * mttkrp_warp_smem<VT>(EPL);
     const int64_t ctiles = ceil_div(R, G * EPL);
     const uint32_t ldc_b = (uint32_t)(ldc * (int64_t)sizeof(VT)), ldd_b = (uint32_t)(ldd * (int64_t)sizeof(VT));
     const VT *v = static_cast<const VT *>(B->vals);
@@ -267,7 +284,7 @@ static spd_status launch_mttkrp_g(const spd_csf3 *B, const void *C, int64_t ldc,
         if (P > B->dim0) P = B->dim0;
         if (P < 1) P = 1;
         dim3 grid((unsigned)ceil_div(P, wpb), (unsigned)ctiles);
-        spmttkrp_warp_kernel<VT, EPL, G><<<grid, threads, 0, st>>>(
+        spmttkrp_warp_kernel<VT, EPL, G><<<grid, threads, smem, st>>>(
             B->dim0, B->nfib, B->pos1, B->crd1, B->pos2, B->crd2, v, cc, ldc_b, dd, ldd_b, R, aa, lda, nullptr,
             nullptr, nullptr, 0, P, nullptr, nullptr);
         return check_launch("spmttkrp_warp_kernel(row)");
@@ -285,7 +302,7 @@ static spd_status launch_mttkrp_g(const spd_csf3 *B, const void *C, int64_t ldc,
                                                                                      Lw.npieces, psl);
     if ((s = check_launch("slice_partition_kernel"))) return s;
     dim3 grid((unsigned)ceil_div(Lw.npieces, wpb), (unsigned)ctiles);
-    spmttkrp_warp_kernel<VT, EPL, G><<<grid, threads, 0, st>>>(
+    spmttkrp_warp_kernel<VT, EPL, G><<<grid, threads, smem, st>>>(
         B->dim0, B->nfib, B->pos1, B->crd1, B->pos2, B->crd2, v, cc, ldc_b, dd, ldd_b, R, aa, lda, pfib, ppos, psl,
         Lw.npieces, 0, crow, cval);
     if ((s = check_launch("spmttkrp_warp_kernel(nnz)"))) return s;

@@ -31,7 +31,7 @@ namespace spd {
 constexpr unsigned FULLM = 0xffffffffu;
 
 template <typename VT, int EPL, int G, int KT>
-__global__ void __launch_bounds__(256) sddmm_warp_kernel(
+__global__ void __launch_bounds__(kWarpBlockMax) sddmm_warp_kernel(
     int64_t n, const int32_t *__restrict__ pos, const int32_t *__restrict__ crd, const VT *__restrict__ vals,
     const VT *__restrict__ C, int64_t ldc, const VT *__restrict__ Dnk, int64_t ldd, int64_t K, uint32_t ldc_b,
     uint32_t ldd_b, typename Traits<VT>::out *__restrict__ out, const int32_t *__restrict__ prow,
@@ -40,16 +40,15 @@ __global__ void __launch_bounds__(256) sddmm_warp_kernel(
     using OT = typename Traits<VT>::out;
     constexpr int NPG = 32 / G;                             // positions per warp step
     constexpr int U = 4;                                    // warp steps in flight
-    __shared__ int32_t s_crd_all[8][32], s_row_all[8][32];  // one window per warp (<= 8 warps)
-    __shared__ AT s_val_all[8][32];
+    extern __shared__ __align__(16) unsigned char sddmm_smem[];  // one window per warp
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
     const int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid;
     if (c >= (prow ? npieces : P)) return;
     const PieceBounds b = prow ? nnz_piece(c, prow, ppos) : row_piece(c, P, n, pos);
-    int32_t *s_crd = s_crd_all[wid];
-    int32_t *s_row = s_row_all[wid];
-    AT *s_val = s_val_all[wid];
+    int32_t *s_crd = reinterpret_cast<int32_t *>(sddmm_smem) + wid * 64;  // crd [32], row [32]
+    int32_t *s_row = s_crd + 32;
+    AT *s_val = reinterpret_cast<AT *>(sddmm_smem + (blockDim.x >> 5) * 64 * sizeof(int32_t)) + wid * 32;
     const int gi = lane / G;  // group of this lane
     const int gl = lane % G;  // lane inside the group
     bool writer;
@@ -188,7 +187,7 @@ __device__ __forceinline__ void mma_bf16_16816(float (&d)[4], uint32_t a0, uint3
         : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
-__global__ void __launch_bounds__(256) sddmm_mma_kernel(
+__global__ void __launch_bounds__(kWarpBlockMax) sddmm_mma_kernel(
     int64_t n, const int32_t *__restrict__ pos, const int32_t *__restrict__ crd,
     const __nv_bfloat16 *__restrict__ vals, const __nv_bfloat16 *__restrict__ C, uint32_t ldc_b,
     const __nv_bfloat16 *__restrict__ Dnk, uint32_t ldd_b, int64_t K, float *__restrict__ out,
@@ -296,7 +295,7 @@ static spd_status launch_sddmm_mma(const spd_csr *B, const void *C, int64_t K, i
                                    int64_t ldd, void *outv, int split, const Tuning &tn, void *ws, cudaStream_t st) {
     using BT = __nv_bfloat16;
     const uint32_t ldc_b = (uint32_t)(ldc * 2), ldd_b = (uint32_t)(ldd * 2);
-    const int threads = tn.block_threads > 256 ? 256 : tn.block_threads;
+    const int threads = tn.block_threads;
     const int wpb = threads / 32;
     const BT *v = static_cast<const BT *>(B->vals);
     const BT *cc = static_cast<const BT *>(C);
@@ -325,8 +324,10 @@ static spd_status launch_sddmm_g(const spd_csr *B, const void *C, int64_t K, int
                                  int64_t ldd, void *outv, int split, const Tuning &tn, void *ws, cudaStream_t st) {
     using OT = typename Traits<VT>::out;
     const uint32_t ldc_b = (uint32_t)(ldc * (int64_t)sizeof(VT)), ldd_b = (uint32_t)(ldd * (int64_t)sizeof(VT));
-    const int threads = tn.block_threads > 256 ? 256 : tn.block_threads;  // shared windows for <= 8 warps
+    using AT = typename Traits<VT>::acc;
+    const int threads = tn.block_threads;
     const int wpb = threads / 32;
+    const size_t smem = (size_t)wpb * 32 * (2 * sizeof(int32_t) + sizeof(AT));
     const VT *v = static_cast<const VT *>(B->vals);
     const VT *cc = static_cast<const VT *>(C);
     const VT *dd = static_cast<const VT *>(Dnk);
@@ -334,7 +335,7 @@ static spd_status launch_sddmm_g(const spd_csr *B, const void *C, int64_t K, int
     if (split == SPD_SPLIT_ROW) {
         int64_t P = tn.row_pieces > 0 ? tn.row_pieces : ceil_div(B->nrows + B->nnz, tn.unit_items);
         if (P < 1) P = 1;
-        sddmm_warp_kernel<VT, EPL, G, KT><<<(unsigned)ceil_div(P, wpb), threads, 0, st>>>(
+        sddmm_warp_kernel<VT, EPL, G, KT><<<(unsigned)ceil_div(P, wpb), threads, smem, st>>>(
             B->nrows, B->pos, B->crd, v, cc, ldc, dd, ldd, K, ldc_b, ldd_b, o, nullptr, nullptr, 0, P);
         return check_launch("sddmm_warp_kernel(row)");
     }
@@ -344,7 +345,7 @@ static spd_status launch_sddmm_g(const spd_csr *B, const void *C, int64_t K, int
     int32_t *ppos = reinterpret_cast<int32_t *>(w + Lw.part_pos);
     spd_status s = launch_merge_partition(B->nrows, B->nnz, B->pos, tn.unit_items, Lw.npieces, prow, ppos, st);
     if (s) return s;
-    sddmm_warp_kernel<VT, EPL, G, KT><<<(unsigned)ceil_div(Lw.npieces, wpb), threads, 0, st>>>(
+    sddmm_warp_kernel<VT, EPL, G, KT><<<(unsigned)ceil_div(Lw.npieces, wpb), threads, smem, st>>>(
         B->nrows, B->pos, B->crd, v, cc, ldc, dd, ldd, K, ldc_b, ldd_b, o, prow, ppos, Lw.npieces, 0);
     return check_launch("sddmm_warp_kernel(nnz)");
 }

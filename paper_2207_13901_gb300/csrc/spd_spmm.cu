@@ -16,7 +16,7 @@ namespace spd {
 constexpr unsigned FULL = kFullMask;
 
 template <typename VT, int EPL, int G, int U, bool FULLTILE, bool ACC>
-__global__ void __launch_bounds__(256, kSpmmMinBlocks) spmm_warp_kernel(
+__global__ void __launch_bounds__(kWarpBlockMax, kSpmmMinBlocks) spmm_warp_kernel(
     int64_t n, const int32_t *__restrict__ pos, const int32_t *__restrict__ crd, const VT *__restrict__ vals,
     const VT *__restrict__ X, uint32_t ldx_bytes, typename Traits<VT>::out *__restrict__ Y, int64_t ldy, int64_t L,
     const int32_t *__restrict__ prow, const int32_t *__restrict__ ppos, int64_t npieces, int64_t P,
@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(256, kSpmmMinBlocks) spmm_warp_kernel(
 // dX(j,l) = A(i,j) * dY(i,l): walk A's rows in the piece, keep the current row of dY in
 // registers and scatter vals[p] * dY(i,:) into row crd[p] of dX with atomic adds.
 template <typename VT, int EPL>
-__global__ void __launch_bounds__(256) spmm_t_warp_kernel(
+__global__ void __launch_bounds__(kWarpBlockMax) spmm_t_warp_kernel(
     int64_t n, const int32_t *__restrict__ pos, const int32_t *__restrict__ crd, const VT *__restrict__ vals,
     const VT *__restrict__ dY, int64_t ldy, typename Traits<VT>::out *__restrict__ dX, int64_t ldx, int64_t L,
     const int32_t *__restrict__ prow, const int32_t *__restrict__ ppos, int64_t npieces, int64_t P) {

@@ -17,9 +17,11 @@ namespace spd {
 constexpr unsigned kFullMask = 0xffffffffu;
 constexpr int32_t kLongRow = 4096;
 
-// Blocks of 256 threads per SM the SpMM kernels must fit: 4 caps them at 64 registers,
-// so 32 warps stay resident to keep enough rows of X in flight.
-constexpr int kSpmmMinBlocks = 4;
+// Warps per SM the SpMM kernels must fit: 32 caps them at 64 registers, so enough rows
+// of X stay in flight. As launch bounds: blocks of up to kWarpBlockMax threads, this
+// many of them resident.
+constexpr int kSpmmResidentWarps = 32;
+constexpr int kSpmmMinBlocks = kSpmmResidentWarps * 32 / kWarpBlockMax;
 
 
 // Window of row ends: lane q holds the end of row rw + q (true_end) while the warp

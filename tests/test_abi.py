@@ -93,8 +93,9 @@ def test_host_side_argument_errors():
     assert lib.spd_spmv(ctypes.byref(A), 4096, 1, 8192, 1, 7, None, None, 0, None) == 10
     t = _abi.spd_tune(33, 0, 0, 0)
     assert lib.spd_spmm(ctypes.byref(A), 4096, 8, 8, 1, 8192, 8, 1, 1, ctypes.byref(t), None, 0, None) == 10
-    t = _abi.spd_tune(0, 0, 512, 0)  # the warp kernels take at most 256 threads per block
-    assert lib.spd_spmm(ctypes.byref(A), 4096, 8, 8, 1, 8192, 8, 1, 1, ctypes.byref(t), None, 0, None) == 10
+    for bt in (544, 1024, 48, 100):  # the warp kernels take 64..512 threads a block, whole warps
+        t = _abi.spd_tune(0, 0, bt, 0)
+        assert lib.spd_spmm(ctypes.byref(A), 4096, 8, 8, 1, 8192, 8, 1, 1, ctypes.byref(t), None, 0, None) == 10
     # missing or short workspace for the nnz split
     assert lib.spd_spmv(ctypes.byref(A), 4096, 1, 8192, 1, 1, None, None, 0, None) == 6
     assert lib.spd_spmm(ctypes.byref(A), 4096, 8, 4, 1, 8192, 8, 1, 1, None, None, 0, None) == 2  # ldx < L

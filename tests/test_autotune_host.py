@@ -15,8 +15,9 @@ def fake_timer(table, calls):
 
 def test_fastest_candidate_is_chosen_and_cached(tmp_path, monkeypatch):
     cands = autotune.warp_candidates(True, inflight=True)
-    # 4 unit sizes x 2 block sizes x 2 in-flight depths, plus the row split
-    assert len(cands) == 17 and cands[-1] == {"split": "row", "tune": None}
+    # 4 unit sizes x 3 block sizes x 2 in-flight depths, plus the row split
+    assert len(cands) == 25 and cands[-1] == {"split": "row", "tune": None}
+    assert {c["tune"]["block_threads"] for c in cands[:-1]} == {128, 256, 512}
     ms = {i: 5.0 + i for i in range(len(cands))}
     ms[6] = 1.25
     calls = []

@@ -54,14 +54,14 @@ def test_batched_policies(dtype, L):
     dmats = [spd.CSR.from_host(A.pos, A.crd, A.vals, (A.nrows, A.ncols), dtype=dtype) for A in mats]
     Xs = [torch.as_tensor(X).to(dtype).cuda() for X in Xh]
     batch = spd.SpMMBatch(dmats, Xs)
-    for policy in ("row", "nnz", "auto"):
-        for unit in (64, 1024):
-            batch.configure(policy, unit)
-            for Y in batch.Ys:
-                Y.fill_(float("nan"))
-            batch.run()
-            torch.cuda.synchronize()
-            check_batch(mats, Xh, batch.Ys, dtype)
+    for policy, unit, threads in (("row", 64, 256), ("row", 1024, 256), ("nnz", 64, 256), ("nnz", 1024, 256),
+                                  ("auto", 64, 256), ("auto", 1024, 256), ("nnz", 64, 512), ("auto", 1024, 64)):
+        batch.configure(policy, unit, threads)
+        for Y in batch.Ys:
+            Y.fill_(float("nan"))
+        batch.run()
+        torch.cuda.synchronize()
+        check_batch(mats, Xh, batch.Ys, dtype)
     # one launch per matrix gives the same products
     for Y in batch.Ys:
         Y.fill_(float("nan"))

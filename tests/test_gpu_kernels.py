@@ -278,6 +278,58 @@ def test_spmm_lane_shapes(name, dtype, L, lane_groups):
               row_lengths(A.pos)[sel][:, None])
 
 
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("block_threads", [64, 512])
+def test_warp_kernels_block_sizes(dtype, block_threads):
+    """The smallest and largest blocks of the warp-per-unit kernels (the per-warp windows
+    live in shared memory sized by the block): SpMM in both lane shapes, SpMM^T, SDDMM
+    in both forms and SpMTTKRP, with many pieces per block and a partial last block."""
+    A = get_mats()["rmat12"]
+    T = get_tens()["zipf"]
+    rng = np.random.default_rng(29)
+    vr = rounded(A.vals, dtype)
+    dA = dev_csr(A, dtype)
+    lens = row_lengths(A.pos)
+    for split, unit in (("nnz", 96), ("nnz", 2048), ("row", 0)):
+        tune = {"block_threads": block_threads}
+        if unit:
+            tune["unit_items"] = unit
+        for L, groups in ((64, 1), (64, 2), (40, 0)):
+            X = rng.uniform(-1, 1, (A.ncols, L))
+            Xr = rounded(X, dtype)
+            ref = oracle.spmm(A.pos, A.crd, vr, Xr, accurate=True)
+            scale = oracle.spmm(A.pos, A.crd, np.abs(vr), np.abs(Xr))
+            Y = spd.spmm(dA, dev(X, dtype), split=split, tune=dict(tune, lane_groups=groups))
+            check(Y.double().cpu().numpy(), ref, scale, dtype, "spmm bt=%d %s L=%d" % (block_threads, tune, L),
+                  lens[:, None])
+        dY = rng.uniform(-1, 1, (A.nrows, 32))
+        dYr = rounded(dY, dtype)
+        ref = oracle.spmm_t(A.pos, A.crd, vr, dYr, A.ncols, accurate=True)
+        scale = oracle.spmm_t(A.pos, A.crd, np.abs(vr), np.abs(dYr), A.ncols)
+        dX = spd.spmm_t(dA, dev(dY, dtype), split=split, tune=tune)
+        check(dX.double().cpu().numpy(), ref, scale, dtype, "spmm_t bt=%d %s" % (block_threads, tune),
+              np.bincount(A.crd, minlength=A.ncols)[:, None])
+        K = 64
+        C = rng.standard_normal((A.nrows, K))
+        Dnk = rng.standard_normal((A.ncols, K))
+        Cr, Dr = rounded(C, dtype), rounded(Dnk, dtype)
+        ref = oracle.sddmm(A.pos, A.crd, vr, Cr, Dr, accurate=True)
+        scale = oracle.sddmm(A.pos, A.crd, np.abs(vr), np.abs(Cr), np.abs(Dr))
+        for form in ((1, 2) if dtype == torch.bfloat16 else (0,)):
+            out = spd.sddmm(dA, dev(C, dtype), dev(Dnk, dtype), split=split, tune=dict(tune, form=form))
+            check(out.double().cpu().numpy(), ref, scale, dtype, "sddmm bt=%d %s form %d" % (block_threads, tune, form),
+                  K, extra=1)
+        R = 32
+        Cm = rng.standard_normal((T.dims[1], R))
+        Dm = rng.standard_normal((T.dims[2], R))
+        tv, Cmr, Dmr = rounded(T.vals, dtype), rounded(Cm, dtype), rounded(Dm, dtype)
+        ref = oracle.spmttkrp(T.pos1, T.crd1, T.pos2, T.crd2, tv, Cmr, Dmr, accurate=True)
+        scale = oracle.spmttkrp(T.pos1, T.crd1, T.pos2, T.crd2, np.abs(tv), np.abs(Cmr), np.abs(Dmr))
+        Am = spd.spmttkrp(dev_csf(T, dtype), dev(Cm, dtype), dev(Dm, dtype), split=split, tune=tune)
+        check(Am.double().cpu().numpy(), ref, scale, dtype, "spmttkrp bt=%d %s" % (block_threads, tune),
+              slice_lengths(T)[:, None], extra=1)
+
+
 # ------------------------------------------------------------------------------ SpMM^T
 
 @pytest.mark.parametrize("name", ["uniform4096", "rmat12", "longrow", "col0", "empty_rows", "no_nnz"])

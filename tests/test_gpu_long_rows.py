@@ -190,7 +190,8 @@ def test_spmttkrp_long_slice(dtype, R):
     scale = oracle.spmttkrp(T.pos1, T.crd1, T.pos2, T.crd2, np.abs(vr), np.abs(Cr), np.abs(Dr))
     slice_len = row_lengths(np.asarray(T.pos2, dtype=np.int64)[np.asarray(T.pos1, dtype=np.int64)])
     dT = spd.CSF3.from_host(T.pos1, T.crd1, T.pos2, T.crd2, T.vals, T.dims, dtype=dtype)
-    for split, tune in [("nnz", None), ("nnz", {"unit_items": 512}), ("row", None)]:
+    for split, tune in [("nnz", None), ("nnz", {"unit_items": 512}), ("row", None),
+                        ("nnz", {"unit_items": 512, "block_threads": 512}), ("row", {"block_threads": 64})]:
         A = spd.spmttkrp(dT, dev(C, dtype), dev(D, dtype), split=split, tune=tune)
         check_error(A.double().cpu().numpy(), ref, scale, dtype == torch.float64, slice_len[:, None],
                     "spmttkrp long slice %s R=%d %s %s" % (dtype, R, split, tune), extra=1)
