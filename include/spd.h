@@ -91,7 +91,14 @@ typedef enum {
     SPD_OP_SPMTTKRP = 5
 } spd_op;
 
-/* A CSR matrix {Dense, Compressed}: nrows x ncols with nnz stored entries.
+/* Largest size of any dimension, count of entries or count of fibers a descriptor may
+ * hold: 2^31 - 2^17 - 1. Indices are int32 and the kernels step through them in windows
+ * and tiles of up to 2^16 items, so every offset they form stays below 2^31. Larger
+ * sizes return SPD_ERR_SHAPE. */
+#define SPD_MAX_INDEX 2147352575LL
+
+/* A CSR matrix {Dense, Compressed}: nrows x ncols with nnz stored entries, each size at
+ * most SPD_MAX_INDEX.
  * pos: int32[nrows+1], crd: int32[nnz], vals: nnz elements of type vtype (device). */
 typedef struct {
     int64_t nrows, ncols, nnz;
@@ -103,7 +110,7 @@ typedef struct {
 } spd_csr;
 
 /* A CSF 3-tensor {Dense, Compressed, Compressed} of shape dim0 x dim1 x dim2 with nfib
- * non-empty fibers (i,j) and nnz stored entries.
+ * non-empty fibers (i,j) and nnz stored entries, each size at most SPD_MAX_INDEX.
  * pos1: int32[dim0+1], crd1: int32[nfib] (j of each fiber),
  * pos2: int32[nfib+1], crd2: int32[nnz] (k of each entry), vals: nnz elements. */
 typedef struct {
@@ -334,7 +341,7 @@ spd_status spd_spadd3_workspace_size(const spd_csr *B, const spd_csr *C, const s
 
 /* Phase 1: a_pos (device int32[nrows + 1], caller-owned) receives A's pos; *nnz_out (host)
  * receives nnz(A) = a_pos[nrows]. Synchronizes `stream` (the size is needed on the host
- * to allocate A). nnz(B) + nnz(C) + nnz(D) must be below 2^31 - 1. */
+ * to allocate A). nnz(B) + nnz(C) + nnz(D) must be at most SPD_MAX_INDEX. */
 spd_status spd_spadd3_symbolic(const spd_csr *B, const spd_csr *C, const spd_csr *D, int split,
                                const spd_tune *tune, int32_t *a_pos, int64_t *nnz_out, void *ws,
                                size_t ws_bytes, void *stream);

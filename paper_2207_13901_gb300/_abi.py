@@ -14,6 +14,7 @@ from . import build as _build
 
 SPD_OK = 0
 SPD_ERR_SHAPE = 2
+SPD_MAX_INDEX = 2**31 - 2**17 - 1  # largest dimension, entry or fiber count of a descriptor
 SPD_F64, SPD_F32, SPD_BF16 = 0, 1, 2
 SPD_SPLIT_ROW, SPD_SPLIT_NNZ, SPD_SPLIT_AUTO = 0, 1, 2
 SPD_OP_SPMV, SPD_OP_SPMM, SPD_OP_SPMM_T, SPD_OP_SDDMM, SPD_OP_SPTTV, SPD_OP_SPMTTKRP = range(6)

@@ -31,8 +31,9 @@ spd_status check_csr(const spd_csr *A, bool need_vals) {
     if (A->nrows < 0 || A->ncols < 0 || A->nnz < 0)
         return fail(SPD_ERR_SHAPE, "negative size (nrows=%lld ncols=%lld nnz=%lld)", (long long)A->nrows,
                     (long long)A->ncols, (long long)A->nnz);
-    if (A->nrows >= INT32_MAX || A->ncols > INT32_MAX || A->nnz >= INT32_MAX)
-        return fail(SPD_ERR_SHAPE, "sizes exceed the int32 index range");
+    if (A->nrows > SPD_MAX_INDEX || A->ncols > SPD_MAX_INDEX || A->nnz > SPD_MAX_INDEX)
+        return fail(SPD_ERR_SHAPE, "sizes exceed SPD_MAX_INDEX (nrows=%lld ncols=%lld nnz=%lld)",
+                    (long long)A->nrows, (long long)A->ncols, (long long)A->nnz);
     if (A->nrows == 0 && A->nnz != 0) return fail(SPD_ERR_SHAPE, "a matrix without rows has no entries");
     if (A->ncols == 0 && A->nnz != 0) return fail(SPD_ERR_SHAPE, "a matrix without columns has no entries");
     if (!A->pos) return fail(SPD_ERR_NULL, "pos is NULL");
@@ -48,9 +49,9 @@ spd_status check_csf3(const spd_csf3 *B) {
     if (!B) return fail(SPD_ERR_NULL, "tensor descriptor is NULL");
     if (B->dim0 < 0 || B->dim1 < 0 || B->dim2 < 0 || B->nfib < 0 || B->nnz < 0)
         return fail(SPD_ERR_SHAPE, "negative size");
-    if (B->dim0 >= INT32_MAX || B->dim1 > INT32_MAX || B->dim2 > INT32_MAX || B->nfib >= INT32_MAX ||
-        B->nnz >= INT32_MAX)
-        return fail(SPD_ERR_SHAPE, "sizes exceed the int32 index range");
+    if (B->dim0 > SPD_MAX_INDEX || B->dim1 > SPD_MAX_INDEX || B->dim2 > SPD_MAX_INDEX ||
+        B->nfib > SPD_MAX_INDEX || B->nnz > SPD_MAX_INDEX)
+        return fail(SPD_ERR_SHAPE, "sizes exceed SPD_MAX_INDEX");
     if ((B->dim0 == 0 || B->dim1 == 0) && B->nfib != 0) return fail(SPD_ERR_SHAPE, "fibers in an empty tensor");
     if ((B->nfib == 0 || B->dim2 == 0) && B->nnz != 0) return fail(SPD_ERR_SHAPE, "entries without fibers");
     if (!B->pos1 || !B->pos2) return fail(SPD_ERR_NULL, "pos1/pos2 is NULL");

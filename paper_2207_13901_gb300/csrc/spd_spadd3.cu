@@ -252,7 +252,8 @@ static spd_status check_spadd3(const spd_csr *B, const spd_csr *C, const spd_csr
                         (long long)m[q]->ncols, (long long)B->nrows, (long long)B->ncols);
         if (m[q]->vtype != B->vtype) return fail(SPD_ERR_DTYPE, "operands differ in value type");
     }
-    if (B->nnz + C->nnz + D->nnz >= INT32_MAX) return fail(SPD_ERR_SHAPE, "nnz(B) + nnz(C) + nnz(D) exceeds int32");
+    if (B->nnz + C->nnz + D->nnz > SPD_MAX_INDEX)
+        return fail(SPD_ERR_SHAPE, "nnz(B) + nnz(C) + nnz(D) exceeds SPD_MAX_INDEX");
     return SPD_OK;
 }
 

@@ -37,6 +37,9 @@ __all__ = [
     "normal",
     "csr_from_coords",
     "csf3_from_coords",
+    "limit_csr",
+    "limit_rows_csr",
+    "limit_csf3",
 ]
 
 
@@ -385,3 +388,90 @@ def zipf_csf3(dims: Sequence[int], nnz: int, s: float = 1.1, seed: int = 0,
     k = uk & ((1 << bits_k) - 1)
     vals = uniform(uk.shape[0], seed + 1)
     return csf3_from_coords((I, J, K), i, j, k, vals)
+
+
+# ------------------------------------------------------------------ size-limit inputs
+#
+# Inputs with as many entries, rows or fibers as the int32 level format admits. Values
+# are small integers in [-3, 3], returned as int8 (exact in binary64, binary32 and
+# bfloat16): with small integer operands every product and every partial sum is an
+# integer far below 2^24, so any summation order gives the exact result and outputs can
+# be compared bit for bit. Columns are uniform and not sorted within a row (the level
+# format does not require it). Arrays are built without full-size int64 temporaries.
+
+
+def _small_ints(rng: np.random.Generator, n: int) -> np.ndarray:
+    return rng.integers(-3, 4, size=n, dtype=np.int8)
+
+
+def _ragged_lengths(rng: np.random.Generator, n: int, total: int, empty_frac: float) -> np.ndarray:
+    """n non-negative int64 lengths summing to exactly total: lognormal shares, about
+    empty_frac of them zero."""
+    w = rng.lognormal(0.0, 1.5, n)
+    w[rng.random(n) < empty_frac] = 0.0
+    if not w.any():
+        w[0] = 1.0
+    lens = np.floor(w * (total / w.sum())).astype(np.int64)
+    short = total - int(lens.sum())  # 0 <= short < number of non-empty entries
+    nz = np.flatnonzero(w)
+    lens[rng.choice(nz, size=short, replace=short > nz.shape[0])] += 1
+    if lens.sum() != total:  # a repeated choice adds more than once; settle the rest on one entry
+        lens[nz[0]] += total - int(lens.sum())
+    return lens
+
+
+def limit_csr(nrows: int, ncols: int, nnz: int, seed: int = 0, long_row: int = 0) -> CSR:
+    """CSR with exactly ``nnz`` entries over ``nrows`` rows of lognormal lengths (about
+    10% empty) and, if ``long_row`` > 0, row nrows // 3 holding ``long_row`` of them;
+    int8 values in [-3, 3]."""
+    rng = _rng(seed)
+    lens = _ragged_lengths(rng, nrows, nnz - long_row, 0.1)
+    if long_row:
+        lens[nrows // 3] += long_row
+    pos = np.zeros(nrows + 1, dtype=np.int32)
+    np.cumsum(lens, out=pos[1:], dtype=np.int32)
+    crd = rng.integers(0, ncols, size=nnz, dtype=np.int32)
+    return CSR(nrows, ncols, pos, crd, _small_ints(rng, nnz))
+
+
+def limit_rows_csr(nrows: int, ncols: int, nnz: int, seed: int = 0) -> CSR:
+    """CSR with ``nrows`` rows (up to the format's limit) and ``nnz`` entries in random
+    rows, the first and last row among them; int8 values in [-3, 3]. ``pos`` is built
+    as a step function of the occupied rows, with no per-row temporary wider than int32."""
+    rng = _rng(seed)
+    rows = np.concatenate([[0, nrows - 1], rng.integers(0, nrows, size=nnz - 2)])
+    u, cnt = np.unique(rows, return_counts=True)
+    # pos[i] = entries in rows < i: 0 up to u[0], then the count before u[k] + 1 ... up to u[k+1]
+    values = np.concatenate([[0], np.cumsum(cnt)]).astype(np.int32)
+    reps = np.diff(np.concatenate([[-1], u, [nrows]]))
+    pos = np.repeat(values, reps)
+    crd = rng.integers(0, ncols, size=nnz, dtype=np.int32)
+    return CSR(nrows, ncols, pos, crd, _small_ints(rng, nnz))
+
+
+def limit_csf3(dims: Sequence[int], nnz: int, seed: int = 0) -> CSF3:
+    """CSF 3-tensor with exactly ``nnz`` entries in fibers of 1 to 3 entries (about nnz/2
+    fibers), the fibers spread over the slices in lognormal counts (about 10% empty
+    slices), uniform j per fiber and k per entry (neither sorted nor distinct within its
+    parent); int8 values in [-3, 3]."""
+    I, J, K = (int(d) for d in dims)
+    rng = _rng(seed)
+    # fiber ends in chunks of 2^24 fibers until one reaches nnz; that fiber is cut there
+    parts = [np.zeros(1, dtype=np.int32)]
+    total = 0
+    while total < nnz:
+        ends = total + np.cumsum(rng.integers(1, 4, size=1 << 24, dtype=np.int64))
+        k = int(np.searchsorted(ends, nnz))
+        if k < ends.shape[0]:
+            ends = ends[:k + 1]
+            ends[k] = nnz
+        parts.append(ends.astype(np.int32))
+        total = int(ends[-1])
+    pos2 = np.concatenate(parts)
+    del parts
+    F = pos2.shape[0] - 1
+    pos1 = np.zeros(I + 1, dtype=np.int32)
+    np.cumsum(_ragged_lengths(rng, I, F, 0.1), out=pos1[1:], dtype=np.int32)
+    crd1 = rng.integers(0, J, size=F, dtype=np.int32)
+    crd2 = rng.integers(0, K, size=nnz, dtype=np.int32)
+    return CSF3((I, J, K), pos1, crd1, pos2, crd2, _small_ints(rng, nnz))

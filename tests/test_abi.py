@@ -70,6 +70,35 @@ def _csr(nrows=4, ncols=5, nnz=6, vtype=_abi.SPD_F32):
     return _abi.spd_csr(nrows, ncols, nnz, 256, 512, 1024, vtype, 0)
 
 
+def test_index_limit():
+    """Every size of a descriptor may reach SPD_MAX_INDEX and no further (the size
+    queries check the descriptor on the host; the pointers are never dereferenced)."""
+    with open(os.path.join(ROOT, "include", "spd.h")) as f:
+        assert "#define SPD_MAX_INDEX %dLL" % _abi.SPD_MAX_INDEX in f.read()
+    lib = _abi.load()
+    size = ctypes.c_size_t(0)
+    M = _abi.SPD_MAX_INDEX
+    for nrows, ncols, nnz in ((M, 5, 6), (4, M, 6), (M, M, M)):
+        A = _csr(nrows, ncols, nnz)
+        for op in (_abi.SPD_OP_SPMV, _abi.SPD_OP_SPMM, _abi.SPD_OP_SDDMM):
+            assert lib.spd_csr_workspace_size(op, ctypes.byref(A), _abi.SPD_SPLIT_NNZ, 8, None, ctypes.byref(size)) == 0
+    for nrows, ncols, nnz in ((M + 1, 5, 6), (4, M + 1, 6), (4, 5, M + 1), (2**31 - 1, 5, 6)):
+        A = _csr(nrows, ncols, nnz)
+        assert lib.spd_csr_workspace_size(_abi.SPD_OP_SPMV, ctypes.byref(A), _abi.SPD_SPLIT_NNZ, 0, None,
+                                          ctypes.byref(size)) == _abi.SPD_ERR_SHAPE
+        assert b"SPD_MAX_INDEX" in lib.spd_last_error()
+    full = (M, M, M, M, M)
+    B = _abi.spd_csf3(*full, 256, 512, 768, 1024, 2048, _abi.SPD_F32, 0)
+    assert lib.spd_csf3_workspace_size(_abi.SPD_OP_SPMTTKRP, ctypes.byref(B), _abi.SPD_SPLIT_NNZ, 8, None,
+                                       ctypes.byref(size)) == 0
+    for k in range(5):
+        dims = list(full)
+        dims[k] = M + 1
+        B = _abi.spd_csf3(*dims, 256, 512, 768, 1024, 2048, _abi.SPD_F32, 0)
+        assert lib.spd_csf3_workspace_size(_abi.SPD_OP_SPTTV, ctypes.byref(B), _abi.SPD_SPLIT_NNZ, 0, None,
+                                           ctypes.byref(size)) == _abi.SPD_ERR_SHAPE
+
+
 def test_host_side_argument_errors():
     lib = _abi.load()
     size = ctypes.c_size_t(0)

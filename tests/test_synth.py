@@ -71,3 +71,30 @@ def test_shifted_csr_rotates_each_row():
         for i in range(A.nrows):
             got = S.crd[S.pos[i]:S.pos[i + 1]]
             assert np.array_equal(got, np.sort((A.crd[A.pos[i]:A.pos[i + 1]] + shift) % A.ncols))
+
+
+def test_limit_generators_invariants():
+    """The size-limit generators at small sizes: exact entry counts, valid level
+    format, int8 values in [-3, 3], the long row, the forced first and last rows, and
+    fibers of 1 to 3 entries across chunk boundaries of the fiber draw."""
+    A = spd_synth.limit_csr(1000, 77, 100000, seed=1, long_row=20000)
+    lens = np.diff(A.pos)
+    assert A.pos[0] == 0 and A.pos[-1] == 100000 and lens.min() >= 0 and lens[333] >= 20000
+    assert 0.05 < np.mean(lens == 0) < 0.2
+    assert A.crd.dtype == np.int32 and 0 <= A.crd.min() and A.crd.max() < 77
+    assert A.vals.dtype == np.int8 and A.vals.min() == -3 and A.vals.max() == 3
+    B = spd_synth.limit_rows_csr(10**6, 50, 5000, seed=2)
+    assert B.pos.shape[0] == 10**6 + 1 and B.pos[0] == 0 and B.pos[-1] == 5000 and np.diff(B.pos).min() >= 0
+    assert B.pos[1] >= 1 and B.pos[-2] < 5000  # rows 0 and n-1 hold entries
+    rows = np.repeat(np.arange(10**6), np.diff(B.pos))
+    assert rows.shape[0] == 5000 and np.all(np.diff(rows) >= 0)
+    for nnz in (1, 3, 100001, 3 * (1 << 24) + 5):
+        T = spd_synth.limit_csf3((500, 40, 60), nnz, seed=3)
+        d = np.diff(T.pos2)
+        assert T.pos2[0] == 0 and T.pos2[-1] == nnz and d.min() >= 1 and d.max() <= 3
+        assert T.pos1[0] == 0 and T.pos1[-1] == T.nfib and np.diff(T.pos1).min() >= 0
+        assert T.crd1.max() < 40 and T.crd2.max() < 60 and T.crd2.shape[0] == nnz
+    first = spd_synth.limit_csf3((500, 40, 60), 100001, seed=3)
+    again = spd_synth.limit_csf3((500, 40, 60), 100001, seed=3)
+    for name in ("pos1", "crd1", "pos2", "crd2", "vals"):
+        assert np.array_equal(getattr(first, name), getattr(again, name))
