@@ -692,6 +692,11 @@ def run_gpu(args):
                 "unit": "GB/s",
                 "frac": round(spmm_gbs / hbm, 4),
                 "traffic": (spmm_rec or {}).get("dram_bytes"),
+                # the recorded DRAM bytes of the warp kernel over the whole call's mean time
+                # (partition and fix-up included, so a lower bound on the kernel's own rate)
+                "traffic_achieved": round(spmm_rec["dram_bytes"] / (spmm_ms * 1e-3) / 1e9, 1) if spmm_rec else None,
+                "traffic_frac": round(spmm_rec["dram_bytes"] / (spmm_ms * 1e-3) / 1e9 / hbm, 4) if spmm_rec else None,
+                "traffic_per_algorithmic_byte": round(spmm_rec["dram_bytes"] / spmm_bytes, 3) if spmm_rec else None,
                 "l2_hit_pct": (spmm_rec or {}).get("l2_hit_pct"),
                 "traffic_source": "profiles/traffic.json (ncu dram__bytes_read.sum + dram__bytes_write.sum and "
                                   "lts__t_sector_hit_rate.pct of one spmm_warp_kernel launch on this workload)",

@@ -8,10 +8,10 @@ kernels behind the C ABI of include/spd.h. PyTorch supplies memory and streams.
 from .ops import (CSF3, CSR, ColumnBlocks, CSRTranspose, checked, column_blocks, csf3_workspace_size, csr_workspace_size,
                   gather_vals, partition, result_dtype, sddmm, set_checked, spadd3, spadd3_numeric, spadd3_symbolic, spmm,
                   spmm_accumulate, spmm_column_blocked, spmm_t, spmttkrp, spmv, spttv, transpose, validate)
-from . import autograd, batched
+from . import autograd, autotune, batched
 from .batched import SpMMBatch
 
 __all__ = ["CSR", "CSF3", "CSRTranspose", "spmv", "spmm", "spmm_t", "sddmm", "spttv", "spmttkrp", "validate",
            "partition", "set_checked", "checked", "transpose", "gather_vals", "spadd3", "spadd3_symbolic",
            "spadd3_numeric", "ColumnBlocks", "column_blocks", "spmm_accumulate", "spmm_column_blocked",
-           "csr_workspace_size", "csf3_workspace_size", "result_dtype", "autograd", "batched", "SpMMBatch"]
+           "csr_workspace_size", "csf3_workspace_size", "result_dtype", "autograd", "autotune", "batched", "SpMMBatch"]
