@@ -8,6 +8,8 @@ integer far below 2^24 and any summation order is exact: complete outputs are co
 bit for bit with integer sums computed on the host in int64, and sampled rows, positions
 and slices with the oracle, run on the sub-structure that holds them (rows and slices
 are independent, so the oracle's result for them is the same as on the whole input)."""
+import functools
+
 import numpy as np
 import pytest
 import torch
@@ -66,6 +68,12 @@ def sub_rows(pos, crd, vals, rows):
     return sp.astype(np.int32), crd[idx], vals[idx].astype(np.float64), idx
 
 
+@functools.lru_cache(maxsize=1)
+def limit_entries_matrix():
+    """SPD_MAX_INDEX entries over 2^21 ragged rows (one of 2^27 entries), generated once."""
+    return spd_synth.limit_csr(1 << 21, 1 << 16, M, seed=11, long_row=1 << 27)
+
+
 def device_csr(A, dtype):
     vals = torch.from_numpy(A.vals).cuda().to(dtype)
     return spd.CSR(torch.from_numpy(A.pos).cuda(), torch.from_numpy(A.crd).cuda(), vals, (A.nrows, A.ncols))
@@ -77,7 +85,7 @@ def test_limit_entries_csr():
     (K = 32) on the positions of sampled rows, the last rows and both ends of the long row."""
     need_memory(48, 48)
     n, m = 1 << 21, 1 << 16
-    A = spd_synth.limit_csr(n, m, M, seed=11, long_row=1 << 27)
+    A = limit_entries_matrix()
     assert A.nnz == M and int(A.pos[-1]) == M
     x = small_ints(m, 12)
     y_dev = {}
@@ -128,6 +136,47 @@ def test_limit_entries_csr():
         want = oracle.sddmm(np.array([0, hi - lo], dtype=np.int32), A.crd[lo:hi], A.vals[lo:hi].astype(np.float64),
                             C[long_r:long_r + 1].astype(np.float64), Dnk.astype(np.float64))
         assert np.array_equal(out[lo:hi].double().cpu().numpy(), want), ("sddmm long row", lo)
+
+
+def test_limit_entries_transpose():
+    """The transposed structure of the SPD_MAX_INDEX-entry matrix (a stable radix sort of
+    2^31 - 2^17 - 1 positions by column) and the SpMM gradient dX = A^T dY (L = 8) by
+    atomic scatter and over that structure. Checked as properties, with torch on the
+    device: column counts against the host's, every entry of A^T in the right column with
+    the right row, positions ascending inside each column; the two dX schedules agree bit
+    for bit (integer data) and their column sums equal the row sums of A weighted by dY."""
+    need_memory(48, 160)
+    A = limit_entries_matrix()
+    n, m = A.nrows, A.ncols
+    dA = device_csr(A, torch.float32)
+    T = spd.transpose(dA)
+    counts = np.zeros(m, dtype=np.int64)
+    for p0 in range(0, M, 1 << 27):
+        counts += np.bincount(A.crd[p0:min(p0 + (1 << 27), M)], minlength=m)
+    want_tpos = np.concatenate([[0], np.cumsum(counts)])
+    assert np.array_equal(T.t_pos.cpu().numpy().astype(np.int64), want_tpos)
+    perm = T.perm.long()
+    col = torch.repeat_interleave(torch.arange(m, device="cuda", dtype=torch.int32), torch.from_numpy(counts).cuda())
+    assert torch.equal(dA.crd[perm], col)  # every entry of A^T sits in its column
+    # stable: A's order inside a column
+    assert bool(torch.all((T.perm[1:] > T.perm[:-1]) | (col[1:] != col[:-1])))
+    del col
+    rows = torch.repeat_interleave(torch.arange(n, device="cuda", dtype=torch.int32),
+                                   torch.from_numpy(np.diff(A.pos).astype(np.int64)).cuda())
+    assert torch.equal(T.t_crd, rows[perm])  # and carries its row
+    del rows, perm
+    torch.cuda.empty_cache()
+    L = 8
+    dY = small_ints((n, L), 17)
+    ddY = torch.from_numpy(dY).cuda().float()
+    dX_atomic = spd.spmm_t(dA, ddY, split="nnz")
+    dX_t = spd.spmm(T.matrix(dA.vals), ddY, split="nnz")  # an SpMM over A^T (65536 rows of about 2^15)
+    assert torch.equal(dX_atomic, dX_t)
+    rowsum = np.zeros(n, dtype=np.int64)  # sum of the values of each row
+    for r0, r1 in row_chunks(A.pos):
+        rowsum[r0:r1] = segment_sums(A.pos, A.crd, A.vals, np.ones(m, dtype=np.int64), r0, r1)
+    want = rowsum.astype(np.float64) @ dY.astype(np.float64)
+    assert np.array_equal(dX_atomic.double().cpu().numpy().sum(axis=0), want)
 
 
 def test_limit_rows_csr():
