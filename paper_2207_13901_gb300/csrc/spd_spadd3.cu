@@ -37,7 +37,7 @@ __global__ void pos_sum_kernel(int64_t n, Csr3 m, int32_t *__restrict__ psum) {
 __device__ __forceinline__ int32_t lower_bound(const int32_t *a, int32_t lo, int32_t hi, int32_t v) {
     int32_t b = lo, e = hi;
     while (b < e) {
-        const int32_t mid = (b + e) >> 1;
+        const int32_t mid = b + ((e - b) >> 1);  // b + e may pass 2^31 in an operand near the size limit
         if (a[mid] < v) b = mid + 1;
         else e = mid;
     }

@@ -40,6 +40,7 @@ __all__ = [
     "limit_csr",
     "limit_rows_csr",
     "limit_csf3",
+    "limit_interval_csr",
 ]
 
 
@@ -475,3 +476,24 @@ def limit_csf3(dims: Sequence[int], nnz: int, seed: int = 0) -> CSF3:
     crd1 = rng.integers(0, J, size=F, dtype=np.int32)
     crd2 = rng.integers(0, K, size=nnz, dtype=np.int32)
     return CSF3((I, J, K), pos1, crd1, pos2, crd2, _small_ints(rng, nnz))
+
+
+def limit_interval_csr(nrows: int, ncols: int, nnz: int, seed: int = 0) -> CSR:
+    """CSR with exactly ``nnz`` entries whose rows are runs of consecutive columns
+    [o_i, o_i + len_i) at a random offset (sorted and distinct, as SpAdd3's operands must
+    be): lognormal lengths (about 10% empty rows) capped at ``ncols``; int8 values in
+    [-3, 3]. Runs of different operands overlap in part, so a three-way union merges."""
+    rng = _rng(seed)
+    lens = np.minimum(_ragged_lengths(rng, nrows, nnz, 0.1), ncols)
+    short = nnz - int(lens.sum())
+    if short > 0:  # the capped excess goes to the first rows with room
+        room = np.cumsum(ncols - lens)
+        k = int(np.searchsorted(room, short))
+        lens[:k] = ncols
+        lens[k] += short - (int(room[k - 1]) if k else 0)
+    off = (rng.random(nrows) * (ncols - lens + 1)).astype(np.int64)
+    pos = np.zeros(nrows + 1, dtype=np.int32)
+    np.cumsum(lens, out=pos[1:], dtype=np.int32)
+    crd = np.arange(nnz, dtype=np.int32)  # position p of row i gets column o_i + (p - pos[i])
+    crd -= np.repeat((pos[:-1].astype(np.int64) - off).astype(np.int32), lens)
+    return CSR(nrows, ncols, pos, crd, _small_ints(rng, nnz))

@@ -179,6 +179,55 @@ def test_limit_entries_transpose():
     assert np.array_equal(dX_atomic.double().cpu().numpy().sum(axis=0), want)
 
 
+def union_sizes(ops):
+    """Entries of each row of B + C + D for operands whose rows are column runs."""
+    lo = np.stack([A.crd[np.minimum(A.pos[:-1], A.nnz - 1)].astype(np.int64) for A in ops], axis=1)
+    ln = np.stack([np.diff(A.pos).astype(np.int64) for A in ops], axis=1)
+    lo = np.where(ln > 0, lo, 0)
+    hi = lo + ln
+    order = np.argsort(lo, axis=1, kind="stable")
+    lo, hi = np.take_along_axis(lo, order, 1), np.take_along_axis(hi, order, 1)
+    size, reach = np.zeros(lo.shape[0], dtype=np.int64), np.full(lo.shape[0], -1, dtype=np.int64)
+    for k in range(3):
+        start = np.maximum(lo[:, k], reach)
+        size += np.where(hi[:, k] > start, hi[:, k] - start, 0)
+        reach = np.maximum(reach, hi[:, k])
+    return size
+
+
+def test_limit_spadd3():
+    """SpAdd3 with SPD_MAX_INDEX entries in its three operands together, one of them
+    holding all but 2^21 (rows of column runs at random offsets, so the three runs of a
+    row overlap in part): A's pos against the union sizes computed on the host, sampled
+    rows (crd and values) against the oracle, and the sum of A's values against the sum
+    of the operands', for both splits."""
+    need_memory(48, 96)
+    n, m = 1 << 21, 1 << 17
+    ops = [spd_synth.limit_interval_csr(n, m, M - (1 << 21), seed=41),
+           spd_synth.limit_interval_csr(n, m, 1 << 20, seed=42),
+           spd_synth.limit_interval_csr(n, m, 1 << 20, seed=43)]
+    want_pos = np.concatenate([[0], np.cumsum(union_sizes(ops))])
+    want_sum = sum(int(A.vals.astype(np.int64).sum()) for A in ops)
+    rng = np.random.default_rng(44)
+    rows = np.unique(np.concatenate([np.arange(3), rng.integers(0, n, 300), np.arange(n - 100, n)]))
+    subs = []
+    for A in ops:
+        sp, sc, sv, _ = sub_rows(A.pos, A.crd, A.vals, rows)
+        subs.append(spd_synth.CSR(rows.shape[0], m, sp, sc, sv))
+    wp, wc, wv = oracle.spadd3(*subs)
+    dops = [device_csr(A, torch.float32) for A in ops]
+    for split in ("nnz", "row"):
+        S = spd.spadd3(*dops, split=split)
+        got_pos = S.pos.cpu().numpy().astype(np.int64)
+        assert np.array_equal(got_pos, want_pos), split
+        assert float(S.vals.double().sum().item()) == want_sum, split
+        got_idx = np.concatenate([np.arange(got_pos[r], got_pos[r + 1]) for r in rows])
+        assert np.array_equal(S.crd[torch.from_numpy(got_idx).cuda()].cpu().numpy(), wc), split
+        assert np.array_equal(S.vals[torch.from_numpy(got_idx).cuda()].double().cpu().numpy(), wv), split
+        del S
+        torch.cuda.empty_cache()
+
+
 def test_limit_rows_csr():
     """SPD_MAX_INDEX rows, 2^22 entries in random rows (the first and last among them):
     SpMV (both forms, both splits) and SpMM (L = 1) on every row that holds entries,

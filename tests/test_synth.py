@@ -98,3 +98,16 @@ def test_limit_generators_invariants():
     again = spd_synth.limit_csf3((500, 40, 60), 100001, seed=3)
     for name in ("pos1", "crd1", "pos2", "crd2", "vals"):
         assert np.array_equal(getattr(first, name), getattr(again, name))
+
+
+def test_limit_interval_csr_rows_are_column_runs():
+    A = spd_synth.limit_interval_csr(3000, 64, 150000, seed=4)  # lengths capped at 64 columns
+    lens = np.diff(A.pos)
+    assert A.pos[-1] == 150000 and lens.max() <= 64 and lens.min() >= 0
+    assert oracle.validate_level(A.nrows, A.ncols, A.pos, A.crd) == (0, -1)
+    for i in range(A.nrows):
+        seg = A.crd[A.pos[i]:A.pos[i + 1]]
+        if seg.shape[0]:
+            assert np.array_equal(seg, np.arange(seg[0], seg[0] + seg.shape[0]))
+    B = spd_synth.limit_interval_csr(1000, 4096, 100000, seed=5)
+    assert B.pos[-1] == 100000 and B.vals.dtype == np.int8
