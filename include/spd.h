@@ -194,6 +194,14 @@ int spd_checked(void);
  * was set. Checked mode performs the same check after every call. Not during a capture. */
 spd_status spd_fault_status(uint32_t *flags, void *stream);
 
+/* Diagnostic of the fault path above (no counterpart in the paper): launches on `stream`
+ * one kernel that waits, with the same bounded wait, for bulk copies that are never
+ * issued, so that the wait gives up after 1 s and records bit 1; spd_fault_status then
+ * reports it. The kernel accesses no memory but its own shared memory and leaves no copy
+ * in flight, so the context stays usable. Asynchronous; returns SPD_ERR_CUDA only if the
+ * launch fails. */
+spd_status spd_probe_bounded_wait(void *stream);
+
 /* -------------------------------------------------------------------- sizes */
 
 /* Workspace bytes that `op` on CSR `A` with `split` needs. `width` is L for SpMM and

@@ -14,6 +14,7 @@ from . import build as _build
 
 SPD_OK = 0
 SPD_ERR_SHAPE = 2
+SPD_ERR_TIMEOUT = 9
 SPD_MAX_INDEX = 2**31 - 2**17 - 1  # largest dimension, entry or fiber count of a descriptor
 SPD_F64, SPD_F32, SPD_BF16 = 0, 1, 2
 SPD_SPLIT_ROW, SPD_SPLIT_NNZ, SPD_SPLIT_AUTO = 0, 1, 2
@@ -88,6 +89,7 @@ SIGNATURES = {
     "spd_set_checked": (_I, [_I]),
     "spd_checked": (ctypes.c_int, []),
     "spd_fault_status": (_I, [ctypes.POINTER(ctypes.c_uint32), _P]),
+    "spd_probe_bounded_wait": (_I, [_P]),
     "spd_csr_workspace_size": (_I, [_I, _CSR, _I, _I64, _TUNE, ctypes.POINTER(ctypes.c_size_t)]),
     "spd_csf3_workspace_size": (_I, [_I, _CSF, _I, _I64, _TUNE, ctypes.POINTER(ctypes.c_size_t)]),
     "spd_csr_validate": (_I, [_CSR, _P, _SZ, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64), _P]),

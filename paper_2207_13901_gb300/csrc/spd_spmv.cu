@@ -37,6 +37,21 @@ spd_status take_device_faults(unsigned int *flags) {
     return SPD_OK;
 }
 
+// Diagnostic of the bounded wait: one thread arms an mbarrier for 16 bytes of bulk copies
+// that are never issued and waits for them with the wait the warp-tile kernels use. The
+// wait gives up after kWaitLimitNs and records kFaultBulkWait in the fault word, as a
+// stalled copy would; the kernel touches no memory but its own shared memory and ends
+// with no copy in flight.
+__global__ void bounded_wait_probe_kernel() {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar);
+        mbar_fence_init();
+        mbar_arrive_expect(&bar, 16);
+        mbar_wait(&bar, 0, &g_spmv_fault);
+    }
+}
+
 // Shared-memory index with one padding word per 32 entries: each thread consumes IPT
 // consecutive entries, so without the skew a warp's 32 threads would fall on only
 // 32/IPT banks.
@@ -590,11 +605,12 @@ static spd_status launch_spmv_warp(int64_t n, int64_t nnz, const int32_t *pos, c
     constexpr int WPB = kSpmvThreads / 32;
     const size_t smem = (size_t)WPB * Lay::bytes;
     auto kern = spmv_warp_kernel<VT, kSpmvWarpIPT, BULK>;
-    static bool attr_set = false;  // the shared memory of binary64 tiles exceeds the 48 KiB default
-    if (!attr_set) {
+    // The shared memory of binary64 tiles exceeds the 48 KiB default. The limit is an
+    // attribute of the function in the current context (a process may use several GPUs
+    // or recreate its context), so it is set on every such launch; the call is cheap.
+    if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return fail(SPD_ERR_CUDA, "spmv_warp_kernel attribute: %s", cudaGetErrorString(e));
-        attr_set = true;
     }
     const VT *v = static_cast<const VT *>(vals);
     const VT *xx = static_cast<const VT *>(x);
@@ -726,6 +742,11 @@ spd_status spd_fault_status(uint32_t *flags, void *stream) {
     *flags = f;
     if (s) return s;
     return f ? fail(SPD_ERR_TIMEOUT, "a kernel's bounded wait for its bulk copies gave up (flags 0x%x)", f) : SPD_OK;
+}
+
+spd_status spd_probe_bounded_wait(void *stream) {
+    bounded_wait_probe_kernel<<<1, 32, 0, as_stream(stream)>>>();
+    return check_launch("bounded_wait_probe_kernel");
 }
 
 spd_status spd_spttv(const spd_csf3 *B, const void *c, int c_type, void *out_vals, int out_type, int split,

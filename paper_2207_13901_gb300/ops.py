@@ -258,6 +258,23 @@ def checked() -> bool:
     return bool(_abi.load().spd_checked())
 
 
+def fault_status(stream=None) -> int:
+    """Synchronizes the stream and returns, then clears, the fault bits that kernels with
+    bounded waits recorded (``spd_fault_status``): 0 when none gave up, bit 1 when a wait
+    for bulk copies ran out (the outputs of that call are unspecified)."""
+    flags = ctypes.c_uint32(0)
+    s = _abi.load().spd_fault_status(ctypes.byref(flags), _stream(stream))
+    if s not in (0, _abi.SPD_ERR_TIMEOUT):
+        _abi.check("spd_fault_status", s)
+    return int(flags.value)
+
+
+def probe_bounded_wait(stream=None) -> None:
+    """Runs a kernel whose bounded wait runs out after about 1 s (``spd_probe_bounded_wait``),
+    to exercise the fault path: ``fault_status`` reports it afterwards."""
+    _abi.check("spd_probe_bounded_wait", _abi.load().spd_probe_bounded_wait(_stream(stream)))
+
+
 def partition(A: CSR, split: str, npieces: int, unit_items: int = 0):
     """The work partition the kernels use, as two int32 device tensors of npieces + 1."""
     lib = _abi.load()
