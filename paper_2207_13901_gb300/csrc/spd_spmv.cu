@@ -106,6 +106,24 @@ __global__ void __launch_bounds__(NT, sizeof(VT) == 2 ? 8 : 6) spmv_tile_kernel(
         if (rem_rows + rem_nnz == 0) break;
         const int nr = (int)(rem_rows < TILE ? rem_rows : TILE);
         const int items = (int)((rem_rows + rem_nnz) < TILE ? (rem_rows + rem_nnz) : TILE);
+        // Binary32 values: crd and vals of the tile's nonzeros are loaded before its row
+        // ends are known, so that their latency overlaps the row-end phase. The tile holds
+        // at most jmax nonzeros; the positions past its actual count (one per row end in
+        // the tile) are loaded again by the next tile, and x is gathered only for the
+        // actual ones. Measured 2.6-6.4% faster in binary32; the other value types spill
+        // with the loads held across the phase, so they load after it.
+        constexpr bool kEarly = sizeof(VT) == 4;
+        int32_t cc[IPT];
+        AT vv[IPT];
+        if (kEarly) {
+            const int jmax = (int)(rem_nnz < TILE ? rem_nnz : TILE);
+#pragma unroll
+            for (int k = 0; k < IPT; ++k) {
+                const int q = tid + k * NT;
+                cc[k] = q < jmax ? ld_stream(crd + p + q) : 0;
+                vv[k] = q < jmax ? (AT)ld_stream(vals + p + q) : (AT)0;
+            }
+        }
         // row ends of the tile, NT rows at a time: a further chunk only while the last row
         // of the previous one still ended inside the tile (a tile of power-law rows holds
         // about a hundred row ends; a run of empty rows can hold up to TILE)
@@ -137,21 +155,19 @@ __global__ void __launch_bounds__(NT, sizeof(VT) == 2 ? 8 : 6) spmv_tile_kernel(
         __syncthreads();
         const int ic = s_wpre[NWORDS];  // row ends in the tile
         const int jc = items - ic;
-        // products of the tile's nonzeros: coalesced crd/vals, gathered x
-        {
-            int32_t cc[IPT];
-            AT vv[IPT];
+        // products of the tile's nonzeros: coalesced crd/vals (unless loaded early), gathered x
+        if (!kEarly) {
 #pragma unroll
             for (int k = 0; k < IPT; ++k) {
-                int q = tid + k * NT;
+                const int q = tid + k * NT;
                 cc[k] = q < jc ? ld_stream(crd + p + q) : 0;
                 vv[k] = q < jc ? (AT)ld_stream(vals + p + q) : (AT)0;
             }
+        }
 #pragma unroll
-            for (int k = 0; k < IPT; ++k) {
-                int q = tid + k * NT;
-                if (q < jc) s_prod[skew(q)] = vv[k] * (AT)ld_gather(x + cc[k]);
-            }
+        for (int k = 0; k < IPT; ++k) {
+            const int q = tid + k * NT;
+            if (q < jc) s_prod[skew(q)] = vv[k] * (AT)ld_gather(x + cc[k]);
         }
         __syncthreads();
         // this thread's IPT items of the tile
