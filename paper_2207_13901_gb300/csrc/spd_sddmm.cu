@@ -68,11 +68,32 @@ __global__ void __launch_bounds__(kWarpBlockMax) sddmm_warp_kernel(
 
     PosRows pr;
     pr.load(b.r0, n, pos, lane);
+    // Binary32: crd/vals of the window are loaded one window ahead, the next window's
+    // loads in flight while this one is consumed (measured 1-5.5% faster; bfloat16
+    // measured slower with it, so the other types load each window as it starts).
+    constexpr bool kPrefetch = sizeof(VT) == 4;
+    int32_t nx_crd = 0;
+    AT nx_val = (AT)1;
+    if (kPrefetch) {
+        nx_crd = lane < b.p1 - b.p0 ? ld_stream(crd + b.p0 + lane) : 0;
+        nx_val = (lane < b.p1 - b.p0 && vals) ? (AT)ld_stream(vals + b.p0 + lane) : (AT)1;
+    }
     for (int32_t pb = b.p0; pb < b.p1; pb += 32) {
         const int cnt = (b.p1 - pb) < 32 ? (b.p1 - pb) : 32;
         const bool valid = lane < cnt;
-        const int32_t my_crd = valid ? ld_stream(crd + pb + lane) : 0;
-        const AT my_val = (valid && vals) ? (AT)ld_stream(vals + pb + lane) : (AT)1;
+        int32_t my_crd;
+        AT my_val;
+        if (kPrefetch) {
+            my_crd = nx_crd;
+            my_val = nx_val;
+            const int32_t pn = pb + 32;
+            const bool vn = lane < b.p1 - pn;
+            nx_crd = vn ? ld_stream(crd + pn + lane) : 0;
+            nx_val = (vn && vals) ? (AT)ld_stream(vals + pn + lane) : (AT)1;
+        } else {
+            my_crd = valid ? ld_stream(crd + pb + lane) : 0;
+            my_val = (valid && vals) ? (AT)ld_stream(vals + pb + lane) : (AT)1;
+        }
         const int32_t my_row = pr.find(pb + lane, valid, n, pos, lane);
         __syncwarp();
         s_crd[lane] = my_crd;
