@@ -69,9 +69,10 @@ __global__ void __launch_bounds__(kWarpBlockMax) sddmm_warp_kernel(
     PosRows pr;
     pr.load(b.r0, n, pos, lane);
     // Binary32: crd/vals of the window are loaded one window ahead, the next window's
-    // loads in flight while this one is consumed (measured 1-5.5% faster; bfloat16
-    // measured slower with it, so the other types load each window as it starts).
-    constexpr bool kPrefetch = sizeof(VT) == 4;
+    // loads in flight while this one is consumed (K=32 and 128 measured 1.5-7% faster).
+    // bfloat16, and binary32 with two k tiles of C kept in registers (K=256: 8% slower),
+    // load each window as it starts.
+    constexpr bool kPrefetch = sizeof(VT) == 4 && KT != 2;
     int32_t nx_crd = 0;
     AT nx_val = (AT)1;
     if (kPrefetch) {
